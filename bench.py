@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark: QP solves/s of the GB300 OSQP path on the Lasso workload.
+
+One step = one whole solve of one QP: load the raw problem data (already in
+HBM) into the solver, Ruiz scaling, ρ vector and Jacobi diagonal, the ADMM
+iterations with PCG linear solves to ε_abs = ε_rel = 1e-3, unscaling.  The
+timed region covers K steps on the device (CUDA events on the solver's
+stream); L2 is flushed by a 256 MB write between steps, outside the events.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead
+(rank 0 only).  Multi-GPU: replicas only — each rank solves its own instance
+of the same workload, no collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1711_08013_gb300 import problems as pb  # noqa: E402
+
+METRIC = "QP solves/s at eps 1e-3 (batched vs plain); ADMM iter/s; p50/p99 solve latency"
+UNIT = "QP solves/s"
+WORKLOADS = {
+    "lasso": (1, "Lasso QP: data matrix 20000x200 at 15% N(0,1), lambda=0.2*|Ad^T b|_inf; "
+                 "variables (x,y,t) n=20400, rows m=20400"),
+    "random": (0, "random QP n=50 m=500, P=MM^T+1e-2 I, A at 15% N(0,1)"),
+    "portfolio": (2, "portfolio QP n=10000 assets k=100 factors, F at 50% N(0,1); "
+                     "variables (x,y) n=10100, rows m=10101"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lasso")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled while the timed region runs
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [a.strip() for a in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.remove(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes of one ADMM launch (stages of the ADMM kernel, each array
+# read or written once per stage; matrix values + column indices + row
+# pointers once per SpMV)
+# ----------------------------------------------------------------------------
+def admm_bytes(n, m, nnz_kn, nnz_a, sv, K, J, C):
+    d = 8
+    kn = nnz_kn * (sv + 4) + 4 * (n + 1)
+    am = nnz_a * (sv + 4) + 4 * (m + 1)
+    R = kn + n * (2 * d + sv) + m * 2 * sv + n * 2 * sv
+    A0 = am + n * 3 * sv + m * d + n * 2 * sv + m * sv
+    B = kn + n * sv + m * sv + n * sv
+    Cc = n * 5 * sv + n * 3 * sv + m * (2 * sv + d) + m * sv
+    A = am + n * 2 * sv + m * d + n * sv + m * sv
+    U = n * (sv + d) + n * 2 * d + m * (sv + 6 * d) + m * (3 * d + 2 * sv)
+    K1 = kn + am + n * (2 * d + sv) + m * (2 * d + 1) + n * 4 * d + m * 3 * d
+    K2 = m * (9 * d + 1) + m * 2 * sv + n * 8 * d
+    a_phases = max(J - K, 0)
+    return K * (R + A0 + U) + J * (B + Cc) + a_phases * A + C * (K1 + K2)
+
+
+def build_problem(args, rank):
+    cfg, desc = WORKLOADS[args.workload]
+    return cfg, desc, pb.config_problem(cfg, instance=rank)
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    cfg, desc, qp = build_problem(args, 0)
+    for _ in range(args.warmup):
+        O.solve(qp)
+    t0 = time.perf_counter()
+    iters = 0
+    for _ in range(args.steps):
+        r = O.solve(qp)
+        iters += r.iter
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": desc, "precision": "fp64", "eps": 1e-3},
+        "admm_iter_per_s": iters / dt,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full solves of the workload, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(args, qp):
+    from oracle import oracle as O
+    O.solve(qp)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        O.solve(qp)
+        k += 1
+        if time.perf_counter() - t0 > 10.0 or k >= 200:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k} full solves (setup + ADMM) of the same workload instance, "
+                      f"{dt:.1f} s, single thread"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1711_08013_gb300 import _binding as B
+    from paper_1711_08013_gb300.solver import Solver
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    cfg, desc, qp = build_problem(args, rank)
+    prec = B.FP64 if args.precision == "fp64" else B.FP32_MIXED
+    stream = torch.cuda.Stream()
+    s = Solver(qp, stream=stream.cuda_stream, precision=prec)
+    n, m = qp.n, qp.m
+    dev = torch.device("cuda", local)
+    Pv = torch.tensor(qp.P.data, dtype=torch.float64, device=dev)
+    Av = torch.tensor(qp.A.data, dtype=torch.float64, device=dev)
+    qd = torch.tensor(qp.q, dtype=torch.float64, device=dev)
+    ld = torch.tensor(qp.l, dtype=torch.float64, device=dev)
+    ud = torch.tensor(qp.u, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    h = s.handle
+
+    def step():
+        B.osqp_load_data_device(h, Pv.data_ptr(), qd.data_ptr(), Av.data_ptr(), ld.data_ptr(),
+                                ud.data_ptr())
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+            B.osqp_solve_async(h)
+        stream.synchronize()
+        res = s.result()
+        if res.status != B.SOLVED:
+            raise SystemExit(f"warm-up solve did not converge: status {res.status}")
+
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        infos = []
+        sampler = ClockSampler(torch.cuda.current_device())
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0, e1, e2 = evs[k]
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            B.osqp_solve_async(h)
+            e2.record(stream)
+            stream.synchronize()
+            infos.append(s.result())
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        if ws > 1:
+            dist.barrier()
+    step_s = [evs[k][0].elapsed_time(evs[k][2]) * 1e-3 for k in range(args.steps)]
+    admm_s = [evs[k][1].elapsed_time(evs[k][2]) * 1e-3 for k in range(args.steps)]
+    total = sum(step_s)
+    iters = sum(r.iter for r in infos)
+    pcg = sum(r.pcg_iters for r in infos)
+    if any(r.status != B.SOLVED for r in infos):
+        raise SystemExit("a timed solve did not converge")
+    if ws > 1:
+        t = torch.tensor([total, float(iters)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_max, iters_all = float(tmax[0]), float(t[1])
+    else:
+        total_max, iters_all = total, float(iters)
+
+    # end to end through the public C ABI with host buffers: pinned host →
+    # device copies of every input, the solve, and a device → host read of
+    # (x, y), timed on the host clock.
+    pin = lambda a: torch.tensor(a, dtype=torch.float64).pin_memory()
+    Ph, Ah, qh, lh, uh = pin(qp.P.data), pin(qp.A.data), pin(qp.q), pin(qp.l), pin(qp.u)
+    xh, yh = torch.empty(n, dtype=torch.float64).pin_memory(), torch.empty(m, dtype=torch.float64).pin_memory()
+    L = B.lib()
+
+    def e2e_step():
+        B.osqp_load_data(h, Ph.data_ptr(), qh.data_ptr(), Ah.data_ptr(), lh.data_ptr(), uh.data_ptr())
+        B.osqp_solve_async(h)
+        rc = L.osqp_get_solution(h, xh.data_ptr(), yh.data_ptr(), None, None)
+        if rc != 0:
+            raise SystemExit(f"osqp_get_solution failed {rc}")
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_dt], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t[0])
+
+    nnz_kn = qp.P_full().nnz + qp.A.nnz
+    sv = 8 if prec == B.FP64 else 4
+    K_avg = iters / args.steps
+    J_avg = pcg / args.steps
+    C_avg = sum((r.iter + 24) // 25 for r in infos) / args.steps
+    bytes_launch = admm_bytes(n, m, nnz_kn, qp.A.nnz, sv, K_avg, J_avg, C_avg)
+    t_admm = statistics.mean(admm_s)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak = json.load(open(peaks_path))["hbm_gbs"]
+        peak_src = "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    achieved = bytes_launch / t_admm / 1e9
+    lat = sorted(step_s)
+    line = {
+        "metric": METRIC,
+        "value": ws * args.steps / total_max,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if prec == B.FP64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "precision": args.precision, "eps": 1e-3,
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "admm_iter_per_s": iters_all / total_max,
+        "p50_ms": 1e3 * lat[len(lat) // 2],
+        "p99_ms": 1e3 * lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))],
+        "admm_iters_per_solve": K_avg,
+        "pcg_iters_per_solve": J_avg,
+        "admm_kernel_ms": 1e3 * t_admm,
+        "roofline": {"bound": "hbm", "kernel": "k_admm_grid", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": bytes_launch},
+        "e2e": {"value": ws * args.steps / e2e_dt, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * (qp.P.nnz + qp.A.nnz + n + 2 * m),
+                "d2h_bytes_per_step": 8 * (n + m)},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, qp)
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * osqp_gb300.h — C ABI of a GB300-native (sm_103a) implementation of the
+ * operator-splitting QP method of Stellato et al., "OSQP: An Operator
+ * Splitting Solver for Quadratic Programs" (arXiv:1711.08013).
+ *
+ *   minimize  ½ xᵀPx + qᵀx   subject to  l ≤ Ax ≤ u          (Eq. pb:qp, §1.1)
+ *
+ * Every step of the solve runs in this library's own CUDA kernels: modified
+ * Ruiz equilibration (Alg. 2, §5.1), the per-constraint ρ vector (§5.2), the
+ * ADMM iteration of Algorithm 1 (§3.2) with the indirect linear solve of
+ * §3.1 — Jacobi-preconditioned conjugate gradients on
+ * (P + σI + AᵀRA) x̃ = σx − q + Aᵀ(Rz − y), z̃ = Ax̃ — the unscaled termination
+ * and infeasibility tests (§3.4 in the scaled form of §5.1), adaptive ρ̄ with
+ * an on-device Jacobi rebuild (§5.2), and unscaling (Eq. pb:scaled_qp).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are CSC (§7): column pointers (n_cols+1), row indices sorted
+ *    and unique within each column, values.  P is given by its upper
+ *    triangle (row ≤ column); A is m × n.  Indices are int32, values FP64.
+ *  - A bound with |value| ≥ 1e20 (or ±INFINITY) is infinite.  Row i is an
+ *    equality row when l_i == u_i exactly (§5.2).
+ *  - Host pointers unless the name says _device.  The library copies all
+ *    inputs; the caller keeps ownership of its arrays.  The solver owns its
+ *    device memory (one allocation, sized at setup) until osqp_cleanup.
+ *  - Every call returns OSQP_OK (0) or a negative OSQP_ERR_* code and never
+ *    aborts; a failed call leaves the solver usable unless it returned
+ *    OSQP_ERR_CUDA or OSQP_ERR_DEVICE.
+ *  - A solver is bound to the CUDA device current at setup and to the stream
+ *    given there (NULL = the legacy default stream).  One host thread per
+ *    solver; different solvers may be used from different threads.
+ */
+#ifndef OSQP_GB300_H
+#define OSQP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define OSQP_OK 0
+#define OSQP_ERR_DIMS (-1)      /* n < 1, m < 0, or sizes that disagree */
+#define OSQP_ERR_CSC (-2)       /* bad pointers / unsorted / out-of-range indices / P not upper */
+#define OSQP_ERR_NONFINITE (-3) /* NaN or Inf in P, A or q; NaN in l or u */
+#define OSQP_ERR_LGTU (-4)      /* some l_i > u_i */
+#define OSQP_ERR_SETTINGS (-5)  /* α ∉ (0,2), ρ ≤ 0, σ ≤ 0, ε < 0, … */
+#define OSQP_ERR_CUDA (-6)      /* a CUDA runtime call failed */
+#define OSQP_ERR_OOM (-7)       /* device allocation failed */
+#define OSQP_ERR_ARG (-8)       /* NULL solver or required pointer */
+#define OSQP_ERR_DEVICE (-9)    /* a device-side wait ran out of time (grid barrier) */
+#define OSQP_ERR_LIMIT (-10)    /* size beyond what this entry point supports */
+
+/* ---- solver status (osqp_info.status) ----------------------------------- */
+#define OSQP_UNSOLVED 0
+#define OSQP_SOLVED 1
+#define OSQP_MAX_ITER 2
+#define OSQP_PRIMAL_INFEASIBLE 3 /* certificate: osqp_get_certificate(prim_inf_y) */
+#define OSQP_DUAL_INFEASIBLE 4   /* certificate: osqp_get_certificate(dual_inf_x) */
+#define OSQP_TIME_LIMIT 5
+#define OSQP_NUMERICAL_ERROR 6   /* non-finite residuals */
+
+/* ---- precision modes ------------------------------------------------------ */
+#define OSQP_PRECISION_FP64 0       /* matrices, PCG and iterates in FP64 */
+#define OSQP_PRECISION_FP32_MIXED 1 /* scaled matrices and PCG vectors in FP32;
+                                       iterates, residual norms, termination,
+                                       ρ ratios and certificates in FP64 */
+
+typedef struct {
+  int32_t n_rows, n_cols, nnz;
+  const int32_t* colptr; /* n_cols + 1 */
+  const int32_t* rowind; /* nnz */
+  const double* val;     /* nnz */
+} osqp_csc;
+
+typedef struct {
+  double rho;                    /* ρ̄⁰ (§5.2), default 0.1 */
+  double sigma;                  /* σ (§5.2), default 1e-6 */
+  double alpha;                  /* relaxation α ∈ (0,2) (§5.2), default 1.6 */
+  double eps_abs, eps_rel;       /* §3.4, defaults 1e-3 (§7) */
+  double eps_pinf, eps_dinf;     /* §3.4, defaults 1e-4 (§7) */
+  double adaptive_rho_tolerance; /* update ρ̄ when ≥ this factor away (§5.2), default 5 */
+  double eps_equil;              /* Alg. 2 stopping tolerance, default 1e-3 */
+  double pcg_tol_fraction;       /* κ: PCG stops at ‖r‖∞ ≤ κ·min(‖r̄_prim‖∞, ‖r̄_dual‖∞)
+                                    of the last check, default 0.15 */
+  double pcg_tol_floor;          /* τ: and never below τ·‖rhs‖∞, default 1e-10; in the
+                                    FP32-mixed mode also never below 1e-5·‖r⁰‖∞ of the
+                                    iteration (its residual is recomputed in FP64 at the
+                                    next ADMM iteration) */
+  double time_limit;             /* seconds of device time for one solve, 0 = none */
+  int32_t max_iter;              /* ADMM iterations, default 4000 */
+  int32_t check_interval;        /* termination checked every k iterations, default 25 */
+  int32_t adaptive_rho;          /* 0/1, default 1 */
+  int32_t scaling_iters;         /* Ruiz passes (0 = no scaling), default 10 */
+  int32_t max_rho_updates;       /* default 20 */
+  int32_t pcg_max_iter;          /* PCG iterations per ADMM iteration, default 100 */
+  int32_t precision;             /* OSQP_PRECISION_*, default FP64 */
+  int32_t warm_start;            /* 1: osqp_solve starts from the current iterates
+                                    (§6); 0: from zero.  Default 1 */
+  int32_t launch;                /* 0 auto, 1 one persistent block, 2 whole-GPU
+                                    cooperative grid */
+} osqp_settings;
+
+typedef struct {
+  int32_t status, iter, pcg_iters, rho_updates, ruiz_passes, launch;
+  double obj_val;    /* ½xᵀPx + qᵀx of the returned x */
+  double prim_res;   /* ‖Ax − z‖∞ at the last check (unscaled, §3.4) */
+  double dual_res;   /* ‖Px + q + Aᵀy‖∞ at the last check (unscaled) */
+  double rho_estimate;
+  double setup_time; /* seconds: scaling, ρ and Jacobi build (device events) */
+  double solve_time; /* seconds: the ADMM iterations and unscaling (device events) */
+} osqp_info;
+
+typedef struct osqp_solver osqp_solver;
+
+/* Fill *s with the defaults of §5.2 and §7 and this library's readings. */
+void osqp_set_default_settings(osqp_settings* s);
+
+/* Text for an OSQP_ERR_* code or an OSQP_* status (static storage). */
+const char* osqp_error_message(int32_t code);
+
+/* §1.1 problem statement and §7 CSC input.  Validates, builds the CSR
+ * structure of [P̄ Āᵀ] and Ā, allocates all device memory, copies the data
+ * and runs Ruiz scaling, the ρ vector and the Jacobi diagonal on the device.
+ * stream: a cudaStream_t or NULL.  On success *out owns the solver. */
+int32_t osqp_setup(osqp_solver** out, const osqp_csc* P_upper, const double* q,
+                   const osqp_csc* A, const double* l, const double* u,
+                   const osqp_settings* settings, void* stream);
+
+/* Run Algorithm 1 to termination on the solver's stream and wait for it;
+ * fills the info returned by osqp_get_solution. */
+int32_t osqp_solve(osqp_solver* s);
+
+/* As osqp_solve, but only enqueues the work on the stream (no host wait).
+ * Results are valid once the stream reaches this point. */
+int32_t osqp_solve_async(osqp_solver* s);
+
+/* §6 "vectors as parameters": new q, l, u (host, NULL = unchanged) are
+ * scaled with the stored D, E, c; equality rows and the ρ vector / Jacobi
+ * diagonal are rebuilt.  The iterates are kept (warm start). */
+int32_t osqp_update_vectors(osqp_solver* s, const double* q, const double* l, const double* u);
+
+/* §6 "matrices as parameters": new values of P (upper) and A in the CSC
+ * order given at setup (host, NULL = unchanged).  Ruiz scaling, ρ and the
+ * Jacobi diagonal are recomputed; no symbolic work is repeated. */
+int32_t osqp_update_matrices(osqp_solver* s, const double* P_val, const double* A_val);
+
+/* Reload every numeric input from HOST memory (same layouts: P_val
+ * nnz(P_upper), q n, A_val nnz(A), l m, u m), rescale and reset the
+ * iterates; enqueued on the solver's stream (the copies are asynchronous
+ * when the host arrays are page-locked).  Inputs are not validated beyond
+ * NULL checks. */
+int32_t osqp_load_data(osqp_solver* s, const double* P_val, const double* q,
+                       const double* A_val, const double* l, const double* u);
+
+/* Reload every numeric input from DEVICE memory (same layouts as above:
+ * P_val nnz(P_upper), q n, A_val nnz(A), l m, u m) and rescale, enqueued on
+ * the solver's stream without a host wait.  Iterates are reset to zero. */
+int32_t osqp_load_data_device(osqp_solver* s, const double* P_val, const double* q,
+                              const double* A_val, const double* l, const double* u);
+
+/* Set ρ̄ (> 0): rebuilds the ρ vector and the Jacobi diagonal on the
+ * device; no refactorisation exists on this path (§3.1, indirect method). */
+int32_t osqp_update_rho(osqp_solver* s, double rho_bar);
+
+/* §6 warm start: x⁰ = D⁻¹x, z⁰ = Āx⁰, y⁰ = cE⁻¹y (host, NULL = zero). */
+int32_t osqp_warm_start(osqp_solver* s, const double* x, const double* y);
+
+/* Copy the last solution (unscaled: x = Dx̄, z = E⁻¹z̄, y = c⁻¹Eȳ) to host
+ * arrays (any may be NULL) and the info of the last solve (also after
+ * osqp_solve_async).  Waits for the stream. */
+int32_t osqp_get_solution(osqp_solver* s, double* x, double* y, double* z, osqp_info* info);
+
+/* Enqueue device-to-device copies of the unscaled x (n) and y (m). */
+int32_t osqp_get_solution_device(osqp_solver* s, double* x_device, double* y_device);
+
+/* Infeasibility certificates of §5.1: c⁻¹Eδȳ (m) and Dδx̄ (n); zero unless
+ * the status is the matching infeasibility. */
+int32_t osqp_get_certificate(osqp_solver* s, double* prim_inf_y, double* dual_inf_x);
+
+/* Release device memory and the solver. */
+int32_t osqp_cleanup(osqp_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OSQP_GB300_H */

@@ -1,0 +1,936 @@
+// Device code of the OSQP ADMM hot path for sm_103a.
+//
+// One implementation of every stage, templated on a "team" that executes it:
+//   GridTeam  — all CTAs of a cooperative launch, one persistent CTA per SM
+//               slot, synchronised by a bounded grid barrier;
+//   BlockTeam — one CTA (used for small problems and for the batched kernel,
+//               where every CTA owns one problem at a time).
+// Stages are separated by team-wide barriers; reductions are published by
+// each CTA and combined after the next barrier in a fixed order, so every
+// thread of every CTA derives bit-identical scalars (α, β, residual norms,
+// termination decisions) without a second barrier or a host round trip.
+//
+// Matrices live in CSR form: Kn = [P̄ Āᵀ] (n rows; column c < n addresses P̄,
+// column n + i addresses Āᵀ) and Ā (m rows).  SpMV uses a host-built row
+// schedule: rows up to `long_thresh` nonzeros are handled by a sub-warp of
+// `group` lanes (a power of two picked from the mean row length), longer rows
+// are cut into 256-nonzero chunks that whole warps reduce and add atomically
+// into outputs zeroed in an earlier stage.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace osqpgb {
+
+constexpr int kThreads = 512;   // threads per CTA of every team kernel
+constexpr int kMaxRed = 32;     // reduction slots
+constexpr int kSmemDoubles = 34 * kMaxRed;
+constexpr int kChunk = 256;     // nonzeros per long-row chunk
+
+constexpr uint8_t kLInf = 1, kUInf = 2, kEq = 4;  // row-type bits
+constexpr double kInfBound = 1e20;
+constexpr double kNormMin = 1e-4, kNormMax = 1e4;  // Ruiz norm clamp
+constexpr double kRhoMin = 1e-6, kRhoMax = 1e6;    // ρ̄ clamp of the adaptive rule
+constexpr double kEqRhoFactor = 1e3;               // ρ_i = 10³ρ̄ on equality rows
+constexpr double kTiny = 1e-30;
+
+enum DevStatus : int { kUnsolved = 0, kSolved = 1, kMaxIter = 2, kPrimInf = 3, kDualInf = 4,
+                       kTimeLimit = 5, kNumErr = 6 };
+enum DevError : int { kDevOk = 0, kDevBarrierTimeout = 1 };
+
+struct Sched {
+  int nrows, group, long_thresh, nchunks, nlong;
+  const int4* chunks;   // (row, begin, end, first-chunk-of-row)
+  const int* long_rows;
+};
+
+struct Barrier {
+  unsigned int count, gen;
+};
+
+// Per-problem scalars shared between launches (global memory).
+struct Scalars {
+  double c, rho_bar;
+  double obj, prim_res, dual_res;
+  int status, iter, pcg_iters, rho_updates, ruiz_passes, checks;
+  int dev_error, pad;
+};
+
+struct Params {
+  double sigma, alpha, eps_abs, eps_rel, eps_pinf, eps_dinf, rho_tol, eps_equil;
+  double pcg_kappa, pcg_floor, pcg_reduce, time_limit_ns;
+  int max_iter, check_interval, adaptive_rho, scaling_iters, max_rho_updates, pcg_max_iter;
+  unsigned long long barrier_timeout_ns;
+};
+
+template <typename T>
+struct Dev {
+  int n, m;
+  const int* kn_rp;
+  const int* kn_ci;
+  T* kn_v;
+  const double* kn_raw;
+  Sched kn;
+  const int* a_rp;
+  const int* a_ci;
+  T* a_v;
+  const double* a_raw;
+  Sched as;
+  const double *q_raw, *l_raw, *u_raw;
+  uint8_t* rtype;
+  double *D, *E, *q, *l, *u, *rho, *rho_inv, *pdiag, *dg, *nrm_n, *nrm_m;
+  T* dinv;
+  double *x, *z, *y, *dx, *dy;
+  double *xt, *zt, *wm, *um;  // x̃, z̃ and the RHS inputs stay FP64 in both modes
+  T *r, *b, *s, *p0, *p1, *Kp, *rt;
+  double *px, *aty, *pdx, *atdy, *ax, *adx, *azt;
+  double *x_out, *y_out, *z_out, *pcert, *dcert;
+  Scalars* sc;
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* a, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+template <bool MAX>
+__device__ __forceinline__ double rop(double a, double b) {
+  return MAX ? fmax(a, b) : a + b;
+}
+
+__device__ __forceinline__ double red_identity(unsigned maxmask, int k) {
+  return ((maxmask >> k) & 1u) ? -INFINITY : 0.0;
+}
+
+// Block-wide reduction of K slots; slot k is a max when bit k of maxmask is
+// set, else a sum.  Result left in sm[32*kMaxRed + k].  All threads call it.
+template <int K>
+__device__ __forceinline__ void block_reduce(const double (&v)[K], unsigned maxmask, double* sm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const bool mx = (maxmask >> k) & 1u;
+    double x = v[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      double y = __shfl_xor_sync(0xffffffffu, x, off);
+      x = mx ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) sm[wid * kMaxRed + k] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool mx = (maxmask >> k) & 1u;
+      double x = lane < nw ? sm[lane * kMaxRed + k] : red_identity(maxmask, k);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        double y = __shfl_xor_sync(0xffffffffu, x, off);
+        x = mx ? fmax(x, y) : x + y;
+      }
+      if (lane == 0) sm[32 * kMaxRed + k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Teams
+// ---------------------------------------------------------------------------
+struct GridTeam {
+  Barrier* bar;
+  int* err;
+  double* part;  // [2][gridDim.x][kMaxRed]
+  double* sm;
+  unsigned long long timeout_ns;
+  int buf;
+
+  __device__ int nthreads() const { return gridDim.x * blockDim.x; }
+  __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+  __device__ int nwarps() const { return gridDim.x * (blockDim.x >> 5); }
+  __device__ int warp() const { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+  __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+
+  // Grid barrier with a bounded wait: a CTA that waits longer than
+  // timeout_ns records kDevBarrierTimeout and leaves the barrier; every CTA
+  // then stops at its next check of the error word.
+  __device__ bool sync() {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      volatile unsigned int* vgen = &bar->gen;
+      const unsigned int g = *vgen;
+      __threadfence();
+      const unsigned int arrived = atomicAdd(&bar->count, 1u);
+      if (arrived == gridDim.x - 1) {
+        atomicExch(&bar->count, 0u);
+        __threadfence();
+        atomicAdd(&bar->gen, 1u);
+      } else {
+        const unsigned long long t0 = gtimer();
+        unsigned int spins = 0;
+        while (*vgen == g) {
+          if ((++spins & 255u) == 0 && gtimer() - t0 > timeout_ns) {
+            atomicExch(err, kDevBarrierTimeout);
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)err == kDevOk;
+  }
+
+  template <int K>
+  __device__ void publish(const double (&v)[K], unsigned maxmask) {
+    block_reduce<K>(v, maxmask, sm);
+    if (threadIdx.x < K)
+      part[((size_t)buf * gridDim.x + blockIdx.x) * kMaxRed + threadIdx.x] =
+          sm[32 * kMaxRed + threadIdx.x];
+  }
+
+  // Combine the partials of the last publish (after a sync).  Every CTA runs
+  // the same fixed-order combination, so all threads see identical values.
+  template <int K>
+  __device__ void collect(double (&out)[K], unsigned maxmask) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = wid; k < K; k += nw) {
+      const bool mx = (maxmask >> k) & 1u;
+      double x = red_identity(maxmask, k);
+      for (int b = lane; b < (int)gridDim.x; b += 32) {
+        double y = __ldcg(&part[((size_t)buf * gridDim.x + b) * kMaxRed + k]);
+        x = mx ? fmax(x, y) : x + y;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        double y = __shfl_xor_sync(0xffffffffu, x, off);
+        x = mx ? fmax(x, y) : x + y;
+      }
+      if (lane == 0) sm[33 * kMaxRed + k] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = sm[33 * kMaxRed + k];
+    buf ^= 1;
+  }
+};
+
+struct BlockTeam {
+  double* sm;
+  __device__ int nthreads() const { return blockDim.x; }
+  __device__ int tid() const { return threadIdx.x; }
+  __device__ int nwarps() const { return blockDim.x >> 5; }
+  __device__ int warp() const { return threadIdx.x >> 5; }
+  __device__ bool leader() const { return threadIdx.x == 0; }
+  __device__ bool sync() {
+    __syncthreads();
+    return true;
+  }
+  template <int K>
+  __device__ void publish(const double (&v)[K], unsigned maxmask) {
+    block_reduce<K>(v, maxmask, sm);
+  }
+  template <int K>
+  __device__ void collect(double (&out)[K], unsigned) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = sm[32 * kMaxRed + k];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Scheduled CSR traversal.  gather(col, val, acc) folds one nonzero into the
+// NV accumulators; the group / warp then combines lanes (sum, or max when
+// MAXR) and on_row(row, acc) runs once per short row, on_chunk(row, first,
+// acc) once per long-row chunk.
+// ---------------------------------------------------------------------------
+template <int NV, bool MAXR, typename AT, typename MT, class Team, class G, class R, class C>
+__device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* __restrict__ rp,
+                                     const int* __restrict__ ci, const MT* __restrict__ va,
+                                     G gather, R on_row, C on_chunk) {
+  const int lane = threadIdx.x & 31;
+  const int Gw = S.group;
+  const int sub = lane & (Gw - 1);
+  const int gpw = 32 / Gw;
+  const int gw = lane / Gw;
+  const unsigned gmask = (Gw == 32) ? 0xffffffffu : (((1u << Gw) - 1u) << (gw * Gw));
+  const int ngroups = tm.nwarps() * gpw;
+  for (int row = tm.warp() * gpw + gw; row < S.nrows; row += ngroups) {
+    const int b = rp[row], e = rp[row + 1];
+    if (e - b > S.long_thresh) continue;
+    AT acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = MAXR ? AT(0) : AT(0);
+    for (int k = b + sub; k < e; k += Gw) gather(ci[k], va[k], acc);
+    for (int off = Gw >> 1; off > 0; off >>= 1) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        AT o = __shfl_xor_sync(gmask, acc[v], off, Gw);
+        acc[v] = MAXR ? (acc[v] > o ? acc[v] : o) : acc[v] + o;
+      }
+    }
+    if (sub == 0) on_row(row, acc);
+  }
+  for (int c = tm.warp(); c < S.nchunks; c += tm.nwarps()) {
+    const int4 ch = S.chunks[c];
+    AT acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = AT(0);
+    for (int k = ch.y + lane; k < ch.z; k += 32) gather(ci[k], va[k], acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        AT o = __shfl_xor_sync(0xffffffffu, acc[v], off);
+        acc[v] = MAXR ? (acc[v] > o ? acc[v] : o) : acc[v] + o;
+      }
+    }
+    if (lane == 0) on_chunk(ch.x, ch.w, acc);
+  }
+}
+
+// Per-entry pass in schedule order: f(row, k) for every nonzero k of the row.
+template <typename MT, class Team, class F>
+__device__ __forceinline__ void foreach_entry(const Team& tm, const Sched& S,
+                                              const int* __restrict__ rp, F f) {
+  const int lane = threadIdx.x & 31;
+  const int Gw = S.group;
+  const int sub = lane & (Gw - 1);
+  const int gpw = 32 / Gw;
+  const int gw = lane / Gw;
+  const int ngroups = tm.nwarps() * gpw;
+  for (int row = tm.warp() * gpw + gw; row < S.nrows; row += ngroups) {
+    const int b = rp[row], e = rp[row + 1];
+    if (e - b > S.long_thresh) continue;
+    for (int k = b + sub; k < e; k += Gw) f(row, k);
+  }
+  for (int c = tm.warp(); c < S.nchunks; c += tm.nwarps()) {
+    const int4 ch = S.chunks[c];
+    for (int k = ch.y + lane; k < ch.z; k += 32) f(ch.x, k);
+  }
+}
+
+template <class Team, typename V>
+__device__ __forceinline__ void zero_long(const Team& tm, const Sched& S, V* buf) {
+  for (int i = tm.tid(); i < S.nlong; i += tm.nthreads()) buf[S.long_rows[i]] = V(0);
+}
+
+__device__ __forceinline__ double ruiz_delta(double nrm) {
+  // δ = 1/√‖M_i‖∞ (Alg. 2); reading: a zero norm gives δ = 1, others are
+  // clamped to [1e-4, 1e4].
+  return nrm == 0.0 ? 1.0 : 1.0 / sqrt(fmin(fmax(nrm, kNormMin), kNormMax));
+}
+
+__device__ __forceinline__ double rho_of(uint8_t t, double rho_bar) {
+  return (t & kEq) ? kEqRhoFactor * rho_bar : rho_bar;
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi diagonal of K = P̄ + σI + ĀᵀRĀ: dg_j = P̄_jj + σ + Σ_i ρ_i Ā_ij²,
+// read from the Āᵀ half of Kn with ρ_i recomputed from the row types so that
+// the stage may run while the ρ vector itself is rewritten.  Long rows are
+// added atomically into dg, which the caller zeroed beforehand; dinv is
+// written for short rows here and for all rows by finish_dinv after a sync.
+// ---------------------------------------------------------------------------
+template <class Team, typename T>
+__device__ __forceinline__ void jacobi_rows(const Team& tm, const Dev<T>& d, double sigma,
+                                            double rho_bar) {
+  const int n = d.n;
+  const uint8_t* __restrict__ rtype = d.rtype;
+  spmv<1, false, double, T>(
+      tm, d.kn, d.kn_rp, d.kn_ci, d.kn_v,
+      [&](int c, T v, double* acc) {
+        if (c >= n) {
+          double vv = (double)v;
+          acc[0] += rho_of(rtype[c - n], rho_bar) * vv * vv;
+        }
+      },
+      [&](int j, double* acc) {
+        double g = d.pdiag[j] + sigma + acc[0];
+        d.dg[j] = g;
+        d.dinv[j] = T(1.0 / g);
+      },
+      [&](int j, int first, double* acc) {
+        atomicAdd(&d.dg[j], acc[0] + (first ? d.pdiag[j] + sigma : 0.0));
+      });
+}
+
+template <class Team, typename T>
+__device__ __forceinline__ void finish_dinv(const Team& tm, const Dev<T>& d) {
+  for (int i = tm.tid(); i < d.kn.nlong; i += tm.nthreads()) {
+    int j = d.kn.long_rows[i];
+    d.dinv[j] = T(1.0 / d.dg[j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 1: modified Ruiz equilibration (Alg. 2, §5.1) computed from the raw
+// data and the running D, E, c, then the scaled matrices and vectors
+// (Eq. pb:scaled_qp), the ρ vector (§5.2) and the Jacobi diagonal.
+// ---------------------------------------------------------------------------
+template <class Team, typename T>
+__device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double rho_bar,
+                            bool reset_iterates) {
+  const int n = d.n, m = d.m, tid = tm.tid(), nth = tm.nthreads();
+  double c = 1.0;
+  for (int j = tid; j < n; j += nth) {
+    d.D[j] = 1.0;
+    d.nrm_n[j] = 0.0;
+    d.pdiag[j] = 0.0;
+    d.dg[j] = 0.0;
+  }
+  for (int i = tid; i < m; i += nth) {
+    d.E[i] = 1.0;
+    d.nrm_m[i] = 0.0;
+    const double lr = d.l_raw[i], ur = d.u_raw[i];
+    d.rtype[i] = (uint8_t)((lr <= -kInfBound ? kLInf : 0) | (ur >= kInfBound ? kUInf : 0) |
+                           (lr == ur ? kEq : 0));
+  }
+  if (!tm.sync()) return false;
+  int passes = 0;
+  for (int pass = 0; pass < P.scaling_iters; ++pass) {
+    // ‖M_j‖∞ for the first n columns of M = [P Aᵀ; A 0] through the rows of
+    // Kn, and for the last m through the rows of Ā.
+    const double cc = c;
+    spmv<2, true, double, double>(
+        tm, d.kn, d.kn_rp, d.kn_ci, d.kn_raw,
+        [&](int col, double v, double* acc) {
+          if (col < n) acc[0] = fmax(acc[0], fabs(v) * d.D[col]);
+          else acc[1] = fmax(acc[1], fabs(v) * d.E[col - n]);
+        },
+        [&](int j, double* acc) { d.nrm_n[j] = d.D[j] * fmax(cc * acc[0], acc[1]); },
+        [&](int j, int, double* acc) {
+          atomic_max_nonneg(&d.nrm_n[j], d.D[j] * fmax(cc * acc[0], acc[1]));
+        });
+    spmv<1, true, double, double>(
+        tm, d.as, d.a_rp, d.a_ci, d.a_raw,
+        [&](int col, double v, double* acc) { acc[0] = fmax(acc[0], fabs(v) * d.D[col]); },
+        [&](int i, double* acc) { d.nrm_m[i] = d.E[i] * acc[0]; },
+        [&](int i, int, double* acc) { atomic_max_nonneg(&d.nrm_m[i], d.E[i] * acc[0]); });
+    if (!tm.sync()) return false;
+    // δ, S ← diag(δ)S, and ‖1 − δ‖∞
+    double dev[1] = {0.0};
+    for (int j = tid; j < n; j += nth) {
+      double dl = ruiz_delta(d.nrm_n[j]);
+      d.nrm_n[j] = 0.0;
+      d.D[j] *= dl;
+      dev[0] = fmax(dev[0], fabs(1.0 - dl));
+    }
+    for (int i = tid; i < m; i += nth) {
+      double dl = ruiz_delta(d.nrm_m[i]);
+      d.nrm_m[i] = 0.0;
+      d.E[i] *= dl;
+      dev[0] = fmax(dev[0], fabs(1.0 - dl));
+    }
+    tm.template publish<1>(dev, 1u);
+    if (!tm.sync()) return false;
+    tm.template collect<1>(dev, 1u);
+    ++passes;
+    // Cost scaling γ = 1/max{mean_j ‖P̄_:,j‖∞, ‖q̄‖∞} with the new D.
+    spmv<1, true, double, double>(
+        tm, d.kn, d.kn_rp, d.kn_ci, d.kn_raw,
+        [&](int col, double v, double* acc) {
+          if (col < n) acc[0] = fmax(acc[0], fabs(v) * d.D[col]);
+        },
+        [&](int j, double* acc) { d.nrm_n[j] = cc * d.D[j] * acc[0]; },
+        [&](int j, int, double* acc) { atomic_max_nonneg(&d.nrm_n[j], cc * d.D[j] * acc[0]); });
+    double qn[1] = {0.0};
+    for (int j = tid; j < n; j += nth) qn[0] = fmax(qn[0], fabs(cc * d.D[j] * d.q_raw[j]));
+    tm.template publish<1>(qn, 1u);
+    if (!tm.sync()) return false;
+    tm.template collect<1>(qn, 1u);
+    double sum[1] = {0.0};
+    for (int j = tid; j < n; j += nth) {
+      sum[0] += d.nrm_n[j];
+      d.nrm_n[j] = 0.0;
+    }
+    tm.template publish<1>(sum, 0u);
+    if (!tm.sync()) return false;
+    tm.template collect<1>(sum, 0u);
+    const double mx = fmax(sum[0] / (double)n, qn[0]);
+    const double gamma = mx < kNormMin ? 1.0 : 1.0 / mx;
+    c *= gamma;
+    if (dev[0] <= P.eps_equil) break;
+  }
+  // Scaled data: P̄ = cDPD, Ā = EAD (in both Kn and Ā), q̄ = cDq, [El, Eu].
+  foreach_entry<double>(tm, d.kn, d.kn_rp, [&](int j, int k) {
+    const int col = d.kn_ci[k];
+    const double v = d.kn_raw[k];
+    double s;
+    if (col < n) {
+      s = c * d.D[j] * v * d.D[col];
+      if (col == j) d.pdiag[j] = s;
+    } else {
+      s = d.E[col - n] * v * d.D[j];
+    }
+    d.kn_v[k] = T(s);
+  });
+  foreach_entry<double>(tm, d.as, d.a_rp,
+                        [&](int i, int k) { d.a_v[k] = T(d.E[i] * d.a_raw[k] * d.D[d.a_ci[k]]); });
+  for (int j = tid; j < n; j += nth) d.q[j] = c * d.D[j] * d.q_raw[j];
+  for (int i = tid; i < m; i += nth) {
+    const uint8_t t = d.rtype[i];
+    d.l[i] = (t & kLInf) ? -INFINITY : d.E[i] * d.l_raw[i];
+    d.u[i] = (t & kUInf) ? INFINITY : d.E[i] * d.u_raw[i];
+    const double rh = rho_of(t, rho_bar);
+    d.rho[i] = rh;
+    d.rho_inv[i] = 1.0 / rh;
+  }
+  if (!tm.sync()) return false;
+  jacobi_rows(tm, d, P.sigma, rho_bar);
+  if (reset_iterates) {
+    for (int j = tid; j < n; j += nth) {
+      d.x[j] = 0.0;
+      d.dx[j] = 0.0;
+      d.xt[j] = 0.0;
+    }
+    for (int i = tid; i < m; i += nth) {
+      d.z[i] = 0.0;
+      d.y[i] = 0.0;
+      d.dy[i] = 0.0;
+      d.zt[i] = 0.0;
+    }
+  }
+  if (!tm.sync()) return false;
+  finish_dinv(tm, d);
+  if (tm.leader()) {
+    d.sc->c = c;
+    d.sc->ruiz_passes = passes;
+    d.sc->rho_bar = rho_bar;
+  }
+  return tm.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Vector update (§6): q̄ = cDq, l̄ = El, ū = Eu with the stored scaling, row
+// types, ρ vector and Jacobi diagonal for the current ρ̄.
+// ---------------------------------------------------------------------------
+template <class Team, typename T>
+__device__ bool refresh_stage(Team& tm, const Dev<T>& d, const Params& P, double rho_bar) {
+  const int n = d.n, m = d.m, tid = tm.tid(), nth = tm.nthreads();
+  const double c = d.sc->c;
+  for (int j = tid; j < n; j += nth) {
+    d.q[j] = c * d.D[j] * d.q_raw[j];
+    d.dg[j] = 0.0;
+  }
+  for (int i = tid; i < m; i += nth) {
+    const double lr = d.l_raw[i], ur = d.u_raw[i];
+    const uint8_t t = (uint8_t)((lr <= -kInfBound ? kLInf : 0) | (ur >= kInfBound ? kUInf : 0) |
+                                (lr == ur ? kEq : 0));
+    d.rtype[i] = t;
+    d.l[i] = (t & kLInf) ? -INFINITY : d.E[i] * lr;
+    d.u[i] = (t & kUInf) ? INFINITY : d.E[i] * ur;
+    const double rh = rho_of(t, rho_bar);
+    d.rho[i] = rh;
+    d.rho_inv[i] = 1.0 / rh;
+  }
+  if (!tm.sync()) return false;
+  jacobi_rows(tm, d, P.sigma, rho_bar);
+  if (!tm.sync()) return false;
+  finish_dinv(tm, d);
+  if (tm.leader()) d.sc->rho_bar = rho_bar;
+  return tm.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2: Algorithm 1 with the indirect linear solve of §3.1.
+// ---------------------------------------------------------------------------
+template <class Team, typename T>
+__device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
+  const int n = d.n, m = d.m, tid = tm.tid(), nth = tm.nthreads();
+  const double sigma = P.sigma, alpha = P.alpha;
+  const double c = d.sc->c;
+  double rho_bar = d.sc->rho_bar;
+  const unsigned long long t_start = gtimer();
+  // Pointers read once (restrict-qualified for the compiler).
+  const int* __restrict__ kn_rp = d.kn_rp;
+  const int* __restrict__ kn_ci = d.kn_ci;
+  const T* __restrict__ kn_v = d.kn_v;
+  const int* __restrict__ a_rp = d.a_rp;
+  const int* __restrict__ a_ci = d.a_ci;
+  const T* __restrict__ a_v = d.a_v;
+  double* __restrict__ x = d.x;
+  double* __restrict__ z = d.z;
+  double* __restrict__ y = d.y;
+  double* __restrict__ xt = d.xt;
+  double* __restrict__ zt = d.zt;
+  double* __restrict__ wm = d.wm;
+  double* __restrict__ um = d.um;
+  T* __restrict__ r = d.r;
+  T* __restrict__ bv = d.b;
+  T* __restrict__ s = d.s;
+  T* __restrict__ Kp = d.Kp;
+  T* __restrict__ rt = d.rt;
+  T* __restrict__ dinv = d.dinv;
+  const double* __restrict__ rho = d.rho;
+  const double* __restrict__ rho_inv = d.rho_inv;
+
+  int status = kUnsolved, k = 0, pcg_total = 0, rho_updates = 0, checks = 0;
+  bool dinv_dirty = false, have_check = false;
+  double rp_bar = 0.0, rd_bar = 0.0, prim_res = NAN, dual_res = NAN, obj = NAN;
+
+  // Right-hand-side inputs of the first iteration from the current iterates.
+  for (int i = tid; i < m; i += nth) {
+    const double rh = rho[i];
+    wm[i] = rh * z[i] - y[i];
+    um[i] = rh * (z[i] - zt[i]) - y[i];
+  }
+  zero_long(tm, d.kn, r);
+  zero_long(tm, d.kn, bv);
+  if (!tm.sync()) return false;
+
+  for (k = 1; k <= P.max_iter; ++k) {
+    // --- R: initial PCG residual r⁰ = b − Kx̃ and b = σx − q̄ + Āᵀ(Rz − y),
+    // using z̃ = Āx̃:  r⁰ = σ(x − x̃) − q̄ − P̄x̃ + Āᵀ(R(z − z̃) − y).  Formed
+    // from FP64 vectors with FP64 accumulation in both modes, so that in the
+    // FP32 mode every ADMM iteration restarts PCG from an accurate residual
+    // (mixed-precision iterative refinement of the linear solve).
+    if (dinv_dirty) {
+      for (int j = tid; j < n; j += nth) dinv[j] = T(1.0 / d.dg[j]);
+      dinv_dirty = false;
+    }
+    spmv<2, false, double, T>(
+        tm, d.kn, kn_rp, kn_ci, kn_v,
+        [&](int col, T v, double* acc) {
+          const double vv = (double)v;
+          if (col < n) {
+            acc[0] -= vv * xt[col];
+          } else {
+            acc[0] += vv * um[col - n];
+            acc[1] += vv * wm[col - n];
+          }
+        },
+        [&](int j, double* acc) {
+          const double bj = sigma * x[j] - d.q[j];
+          r[j] = T(bj - sigma * xt[j] + acc[0]);
+          bv[j] = T(bj + acc[1]);
+        },
+        [&](int j, int first, double* acc) {
+          const double bj = first ? sigma * x[j] - d.q[j] : 0.0;
+          const double xs = first ? sigma * xt[j] : 0.0;
+          atomicAdd(&r[j], T(bj - xs + acc[0]));
+          atomicAdd(&bv[j], T(bj + acc[1]));
+        });
+    if (!tm.sync()) return false;
+
+    // --- A0: s = p = M⁻¹r; t = Ā p computed on the fly; rs, ‖r‖∞, ‖b‖∞
+    T* pc = d.p0;
+    T* pn = d.p1;
+    double red3[3] = {0.0, 0.0, 0.0};
+    for (int j = tid; j < n; j += nth) {
+      const T rj = r[j];
+      const T sj = rj * dinv[j];
+      s[j] = sj;
+      pc[j] = sj;
+      red3[0] += (double)rj * (double)sj;
+      red3[1] = fmax(red3[1], fabs((double)rj));
+      red3[2] = fmax(red3[2], fabs((double)bv[j]));
+    }
+    spmv<1, false, T, T>(
+        tm, d.as, a_rp, a_ci, a_v, [&](int col, T v, T* acc) { acc[0] += v * (r[col] * dinv[col]); },
+        [&](int i, T* acc) { rt[i] = T(rho[i] * (double)acc[0]); },
+        [&](int i, int, T* acc) { atomicAdd(&rt[i], T(rho[i] * (double)acc[0])); });
+    zero_long(tm, d.kn, Kp);
+    tm.template publish<3>(red3, 6u);
+    if (!tm.sync()) return false;
+    tm.template collect<3>(red3, 6u);
+    double rs = red3[0];
+    const double bnorm = red3[2];
+    // PCG accuracy (reading of "up to some predefined accuracy", §3.1).
+    const double tol = fmax(fmax(P.pcg_floor * bnorm, P.pcg_reduce * red3[1]),
+                            have_check ? P.pcg_kappa * fmin(rp_bar, rd_bar) : 0.1 * P.pcg_kappa * bnorm);
+    bool done = !(red3[1] > tol);
+    int j_it = 0;
+    while (!done) {
+      // --- B: Kp = P̄p + σp + Āᵀ(Rt) and pᵀKp
+      double red1[1] = {0.0};
+      spmv<1, false, T, T>(
+          tm, d.kn, kn_rp, kn_ci, kn_v,
+          [&](int col, T v, T* acc) { acc[0] += v * (col < n ? pc[col] : rt[col - n]); },
+          [&](int j, T* acc) {
+            const T kp = T(sigma) * pc[j] + acc[0];
+            Kp[j] = kp;
+            red1[0] += (double)pc[j] * (double)kp;
+          },
+          [&](int j, int first, T* acc) {
+            const T part = acc[0] + (first ? T(sigma) * pc[j] : T(0));
+            atomicAdd(&Kp[j], part);
+            red1[0] += (double)pc[j] * (double)part;
+          });
+      tm.template publish<1>(red1, 0u);
+      if (!tm.sync()) return false;
+      tm.template collect<1>(red1, 0u);
+      if (!(red1[0] > 0.0)) break;  // pᵀKp ≤ 0 only when p vanished (K ≻ 0)
+      const double a = rs / red1[0];
+      const T aT = T(a);
+      // --- C: x̃ += αp, r −= αKp, s = M⁻¹r, z̃ += αt
+      double red2[2] = {0.0, 0.0};
+      for (int j = tid; j < n; j += nth) {
+        xt[j] += a * (double)pc[j];
+        const T rj = r[j] - aT * Kp[j];
+        r[j] = rj;
+        const T sj = rj * dinv[j];
+        s[j] = sj;
+        red2[0] += (double)rj * (double)sj;
+        red2[1] = fmax(red2[1], fabs((double)rj));
+      }
+      for (int i = tid; i < m; i += nth) {
+        zt[i] += a * rho_inv[i] * (double)rt[i];
+        if (a_rp[i + 1] - a_rp[i] > d.as.long_thresh) rt[i] = T(0);
+      }
+      tm.template publish<2>(red2, 2u);
+      if (!tm.sync()) return false;
+      tm.template collect<2>(red2, 2u);
+      ++j_it;
+      ++pcg_total;
+      if (!(red2[1] > tol) || j_it >= P.pcg_max_iter) break;
+      const double beta = red2[0] / rs;
+      rs = red2[0];
+      const T bT = T(beta);
+      // --- A: p ← s + βp (new buffer), t = Āp on the fly
+      for (int j = tid; j < n; j += nth) pn[j] = s[j] + bT * pc[j];
+      spmv<1, false, T, T>(
+          tm, d.as, a_rp, a_ci, a_v,
+          [&](int col, T v, T* acc) { acc[0] += v * (s[col] + bT * pc[col]); },
+          [&](int i, T* acc) { rt[i] = T(rho[i] * (double)acc[0]); },
+          [&](int i, int, T* acc) { atomicAdd(&rt[i], T(rho[i] * (double)acc[0])); });
+      zero_long(tm, d.kn, Kp);
+      if (!tm.sync()) return false;
+      T* tmp = pc;
+      pc = pn;
+      pn = tmp;
+    }
+    // A long-row entry of rt may still hold this iteration's value when PCG
+    // stopped after stage B: clear it for the next A0.
+    for (int i = tid; i < d.as.nlong; i += nth) rt[d.as.long_rows[i]] = T(0);
+
+    // --- U: Algorithm 1 steps 5–7, y in the form ρ(v − Π(v)) of Eq. (zy-update)
+    for (int j = tid; j < n; j += nth) {
+      const double xn = alpha * xt[j] + (1.0 - alpha) * x[j];
+      d.dx[j] = xn - x[j];
+      x[j] = xn;
+    }
+    for (int i = tid; i < m; i += nth) {
+      const double rh = rho[i];
+      const double zti = zt[i];
+      const double v = alpha * zti + (1.0 - alpha) * z[i] + rho_inv[i] * y[i];
+      const double zn = fmin(fmax(v, d.l[i]), d.u[i]);
+      const double yn = rh * (v - zn);
+      d.dy[i] = yn - y[i];
+      z[i] = zn;
+      y[i] = yn;
+      wm[i] = rh * zn - yn;
+      um[i] = rh * (zn - zti) - yn;
+    }
+    zero_long(tm, d.kn, r);
+    zero_long(tm, d.kn, bv);
+    const bool check = (k % P.check_interval == 0) || (k == P.max_iter);
+    if (check) {
+      zero_long(tm, d.kn, d.px);
+      zero_long(tm, d.kn, d.aty);
+      zero_long(tm, d.kn, d.pdx);
+      zero_long(tm, d.kn, d.atdy);
+      zero_long(tm, d.as, d.ax);
+      zero_long(tm, d.as, d.adx);
+      zero_long(tm, d.as, d.azt);
+    }
+    if (!tm.sync()) return false;
+    if (!check) continue;
+
+    // --- K1: P̄x̄, Āᵀȳ, P̄δx̄, Āᵀδȳ (δȳ projected), Āx̄, Āδx̄, Āx̃ in FP64
+    ++checks;
+    {
+      const uint8_t* __restrict__ rtype = d.rtype;
+      const double* __restrict__ dxp = d.dx;
+      const double* __restrict__ dyp = d.dy;
+      spmv<4, false, double, T>(
+          tm, d.kn, kn_rp, kn_ci, kn_v,
+          [&](int col, T v, double* acc) {
+            const double vv = (double)v;
+            if (col < n) {
+              acc[0] += vv * x[col];
+              acc[2] += vv * dxp[col];
+            } else {
+              const int i = col - n;
+              acc[1] += vv * y[i];
+              double dv = dyp[i];
+              const uint8_t t = rtype[i];
+              if (((t & kUInf) && dv > 0.0) || ((t & kLInf) && dv < 0.0)) dv = 0.0;
+              acc[3] += vv * dv;
+            }
+          },
+          [&](int j, double* acc) {
+            d.px[j] = acc[0];
+            d.aty[j] = acc[1];
+            d.pdx[j] = acc[2];
+            d.atdy[j] = acc[3];
+          },
+          [&](int j, int, double* acc) {
+            atomicAdd(&d.px[j], acc[0]);
+            atomicAdd(&d.aty[j], acc[1]);
+            atomicAdd(&d.pdx[j], acc[2]);
+            atomicAdd(&d.atdy[j], acc[3]);
+          });
+      spmv<3, false, double, T>(
+          tm, d.as, a_rp, a_ci, a_v,
+          [&](int col, T v, double* acc) {
+            const double vv = (double)v;
+            acc[0] += vv * x[col];
+            acc[1] += vv * dxp[col];
+            acc[2] += vv * xt[col];
+          },
+          [&](int i, double* acc) {
+            d.ax[i] = acc[0];
+            d.adx[i] = acc[1];
+            d.azt[i] = acc[2];
+          },
+          [&](int i, int, double* acc) {
+            atomicAdd(&d.ax[i], acc[0]);
+            atomicAdd(&d.adx[i], acc[1]);
+            atomicAdd(&d.azt[i], acc[2]);
+          });
+    }
+    if (!tm.sync()) return false;
+
+    // --- K2: norms of §5.1 (termination, infeasibility) and §5.2 (ρ ratio)
+    double R[24];
+#pragma unroll
+    for (int q = 0; q < 24; ++q) R[q] = 0.0;
+    R[20] = -INFINITY;
+    constexpr unsigned kMaxMask = 0xFFFFFFu & ~((1u << 15) | (1u << 18) | (1u << 21) | (1u << 22));
+    for (int i = tid; i < m; i += nth) {
+      const double Ei = d.E[i], axi = d.ax[i], zi = z[i];
+      R[0] = fmax(R[0], fabs((axi - zi) / Ei));
+      R[1] = fmax(R[1], fabs(axi / Ei));
+      R[2] = fmax(R[2], fabs(zi / Ei));
+      R[3] = fmax(R[3], fabs(axi - zi));
+      R[4] = fmax(R[4], fabs(axi));
+      R[5] = fmax(R[5], fabs(zi));
+      const uint8_t t = d.rtype[i];
+      double dv = d.dy[i];
+      if (((t & kUInf) && dv > 0.0) || ((t & kLInf) && dv < 0.0)) dv = 0.0;
+      R[14] = fmax(R[14], fabs(Ei * dv));
+      if (dv > 0.0) R[15] += d.u[i] * dv;
+      else if (dv < 0.0) R[15] += d.l[i] * dv;
+      const double a = d.adx[i] / Ei;
+      const bool lf = !(t & kLInf), uf = !(t & kUInf);
+      const double viol = (lf && uf) ? fabs(a) : (lf ? -a : (uf ? a : -INFINITY));
+      R[20] = fmax(R[20], viol);
+      // refresh z̃ = Āx̃ and the right-hand-side input that depends on it
+      const double azi = d.azt[i];
+      zt[i] = azi;
+      um[i] = rho[i] * (zi - azi) - y[i];
+    }
+    for (int j = tid; j < n; j += nth) {
+      const double Dj = d.D[j], pxj = d.px[j], atyj = d.aty[j], qj = d.q[j];
+      const double rd = pxj + qj + atyj;
+      R[6] = fmax(R[6], fabs(rd / Dj));
+      R[7] = fmax(R[7], fabs(pxj / Dj));
+      R[8] = fmax(R[8], fabs(atyj / Dj));
+      R[9] = fmax(R[9], fabs(qj / Dj));
+      R[10] = fmax(R[10], fabs(rd));
+      R[11] = fmax(R[11], fabs(pxj));
+      R[12] = fmax(R[12], fabs(atyj));
+      R[13] = fmax(R[13], fabs(qj));
+      R[16] = fmax(R[16], fabs(d.atdy[j] / Dj));
+      const double dxj = d.dx[j];
+      R[17] = fmax(R[17], fabs(Dj * dxj));
+      R[18] += qj * dxj;
+      R[19] = fmax(R[19], fabs(d.pdx[j] / Dj));
+      R[21] += x[j] * pxj;
+      R[22] += qj * x[j];
+    }
+    if (threadIdx.x == 0) R[23] = (double)(gtimer() - t_start);
+    zero_long(tm, d.kn, d.dg);
+    tm.template publish<24>(R, kMaxMask);
+    if (!tm.sync()) return false;
+    tm.template collect<24>(R, kMaxMask);
+    prim_res = R[0];
+    dual_res = R[6] / c;
+    obj = (0.5 * R[21] + R[22]) / c;
+    const double eps_prim = P.eps_abs + P.eps_rel * fmax(R[1], R[2]);
+    const double eps_dual = P.eps_abs + P.eps_rel * fmax(fmax(R[7], R[8]), R[9]) / c;
+    if (!isfinite(prim_res) || !isfinite(dual_res)) {
+      status = kNumErr;
+    } else if (prim_res <= eps_prim && dual_res <= eps_dual) {
+      status = kSolved;
+    } else if (R[16] <= P.eps_pinf * R[14] && R[15] < -P.eps_pinf * R[14]) {
+      status = kPrimInf;
+    } else if (R[19] <= c * P.eps_dinf * R[17] && R[18] < -c * P.eps_dinf * R[17] &&
+               R[20] <= P.eps_dinf * R[17]) {
+      status = kDualInf;
+    } else if (P.time_limit_ns > 0.0 && R[23] > P.time_limit_ns) {
+      status = kTimeLimit;
+    }
+    if (status != kUnsolved) break;
+    rp_bar = R[3];
+    rd_bar = R[10];
+    have_check = true;
+    // ρ̄ adaptation (§5.2) in scaled norms; the Jacobi diagonal is rebuilt
+    // on the device in place of a refactorisation.
+    if (P.adaptive_rho && rho_updates < P.max_rho_updates && k < P.max_iter) {
+      const double pr = R[3] / (fmax(R[4], R[5]) + kTiny);
+      const double dr = R[10] / (fmax(fmax(R[11], R[12]), R[13]) + kTiny);
+      double rn = rho_bar * sqrt(pr / (dr + kTiny));
+      rn = fmin(fmax(rn, kRhoMin), kRhoMax);
+      if (rn > P.rho_tol * rho_bar || rn < rho_bar / P.rho_tol) {
+        rho_bar = rn;
+        ++rho_updates;
+        for (int i = tid; i < m; i += nth) {
+          const double rh = rho_of(d.rtype[i], rho_bar);
+          d.rho[i] = rh;
+          d.rho_inv[i] = 1.0 / rh;
+          wm[i] = rh * z[i] - y[i];
+          um[i] = rh * (z[i] - zt[i]) - y[i];
+        }
+        jacobi_rows(tm, d, sigma, rho_bar);
+        if (!tm.sync()) return false;
+        dinv_dirty = true;
+      }
+    }
+  }
+  if (status == kUnsolved && P.max_iter > 0) status = kMaxIter;
+
+  // --- unscale (Eq. pb:scaled_qp) and certificates (§5.1)
+  for (int j = tid; j < n; j += nth) {
+    d.x_out[j] = d.D[j] * x[j];
+    d.dcert[j] = status == kDualInf ? d.D[j] * d.dx[j] : 0.0;
+  }
+  for (int i = tid; i < m; i += nth) {
+    const double Ei = d.E[i];
+    d.z_out[i] = z[i] / Ei;
+    d.y_out[i] = Ei * y[i] / c;
+    double dv = d.dy[i];
+    const uint8_t t = d.rtype[i];
+    if (((t & kUInf) && dv > 0.0) || ((t & kLInf) && dv < 0.0)) dv = 0.0;
+    d.pcert[i] = status == kPrimInf ? Ei * dv / c : 0.0;
+  }
+  if (tm.leader()) {
+    Scalars* sc = d.sc;
+    sc->status = status;
+    sc->iter = k > P.max_iter ? P.max_iter : k;
+    sc->pcg_iters = pcg_total;
+    sc->rho_updates = rho_updates;
+    sc->checks = checks;
+    sc->rho_bar = rho_bar;
+    sc->obj = obj;
+    sc->prim_res = prim_res;
+    sc->dual_res = dual_res;
+  }
+  // A pending Jacobi rebuild (ρ̄ changed at the last check) is applied now so
+  // that a warm-started solve sees a consistent preconditioner.
+  if (dinv_dirty)
+    for (int j = tid; j < n; j += nth) dinv[j] = T(1.0 / d.dg[j]);
+  return true;
+}
+
+}  // namespace osqpgb

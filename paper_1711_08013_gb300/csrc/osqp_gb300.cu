@@ -1,0 +1,947 @@
+// Host driver and C ABI of the GB300 OSQP library (see include/osqp_gb300.h).
+//
+// Setup (symbolic, host): validate the CSC input, build the CSR structure of
+// Kn = [P̄ Āᵀ] (full symmetric P̄ followed by the column of A that row j of Āᵀ
+// reads) and of Ā, with gather maps from the CSC value arrays, and a row
+// schedule per matrix.  Everything numeric — scattering values, Ruiz
+// scaling, ρ, the Jacobi diagonal, the ADMM/PCG iteration, residuals,
+// unscaling — runs in the kernels of device.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/osqp_gb300.h"
+#include "device.cuh"
+
+using namespace osqpgb;
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_scale_grid(const __grid_constant__ Dev<T> d,
+                                                          const __grid_constant__ Params P,
+                                                          Barrier* bar, int* err, double* part,
+                                                          double rho_bar, int reset) {
+  __shared__ double sm[kSmemDoubles];
+  GridTeam tm{bar, err, part, sm, P.barrier_timeout_ns, 0};
+  scale_stage(tm, d, P, rho_bar, reset != 0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_scale_block(const __grid_constant__ Dev<T> d,
+                                                           const __grid_constant__ Params P,
+                                                           double rho_bar, int reset) {
+  __shared__ double sm[kSmemDoubles];
+  BlockTeam tm{sm};
+  scale_stage(tm, d, P, rho_bar, reset != 0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_refresh_grid(const __grid_constant__ Dev<T> d,
+                                                            const __grid_constant__ Params P,
+                                                            Barrier* bar, int* err, double* part,
+                                                            double rho_bar) {
+  __shared__ double sm[kSmemDoubles];
+  GridTeam tm{bar, err, part, sm, P.barrier_timeout_ns, 0};
+  refresh_stage(tm, d, P, rho_bar);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_refresh_block(const __grid_constant__ Dev<T> d,
+                                                             const __grid_constant__ Params P,
+                                                             double rho_bar) {
+  __shared__ double sm[kSmemDoubles];
+  BlockTeam tm{sm};
+  refresh_stage(tm, d, P, rho_bar);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_admm_grid(const __grid_constant__ Dev<T> d,
+                                                         const __grid_constant__ Params P,
+                                                         Barrier* bar, int* err, double* part) {
+  __shared__ double sm[kSmemDoubles];
+  GridTeam tm{bar, err, part, sm, P.barrier_timeout_ns, 0};
+  admm_stage(tm, d, P);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_admm_block(const __grid_constant__ Dev<T> d,
+                                                          const __grid_constant__ Params P) {
+  __shared__ double sm[kSmemDoubles];
+  BlockTeam tm{sm};
+  admm_stage(tm, d, P);
+}
+
+// raw value gather: dst[k] = src[idx[k]]
+__global__ void k_gather(double* __restrict__ dst, const int* __restrict__ idx,
+                         const double* __restrict__ src, int count) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x)
+    dst[k] = src[idx[k]];
+}
+
+// warm start, part 1: x̄ = D⁻¹x, ȳ = cE⁻¹y, x̃ = x̄, δ = 0
+template <typename T>
+__global__ void k_warm_xy(const __grid_constant__ Dev<T> d, const double* __restrict__ xw,
+                          const double* __restrict__ yw) {
+  const double c = d.sc->c;
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
+    const double xv = xw ? xw[j] / d.D[j] : 0.0;
+    d.x[j] = xv;
+    d.xt[j] = xv;
+    d.dx[j] = 0.0;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) {
+    d.y[i] = yw ? c * yw[i] / d.E[i] : 0.0;
+    d.dy[i] = 0.0;
+  }
+}
+
+// warm start, part 2: z̄ = z̃ = Āx̄ (one warp per row)
+template <typename T>
+__global__ void k_warm_z(const __grid_constant__ Dev<T> d) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = w; i < d.m; i += nw) {
+    double acc = 0.0;
+    for (int k = d.a_rp[i] + lane; k < d.a_rp[i + 1]; k += 32)
+      acc += (double)d.a_v[k] * d.x[d.a_ci[k]];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+      d.z[i] = acc;
+      d.zt[i] = acc;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_zero_iterates(const __grid_constant__ Dev<T> d) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
+    d.x[j] = 0.0;
+    d.dx[j] = 0.0;
+    d.xt[j] = 0.0;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) {
+    d.z[i] = 0.0;
+    d.y[i] = 0.0;
+    d.dy[i] = 0.0;
+    d.zt[i] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SchedHost {
+  int group = 1, long_thresh = 256;
+  std::vector<int4> chunks;
+  std::vector<int> long_rows;
+};
+
+// Row schedule from row-length statistics: rows longer than
+// max(256, 8·mean) are split into kChunk-nonzero chunks; the sub-warp width
+// is the smallest power of two ≥ the mean length of the remaining rows.
+SchedHost make_sched(const std::vector<int>& rp) {
+  SchedHost S;
+  const int nrows = (int)rp.size() - 1;
+  const long long nnz = nrows > 0 ? rp[nrows] : 0;
+  const double mean_all = nrows > 0 ? (double)nnz / nrows : 0.0;
+  S.long_thresh = std::max(256, (int)(8.0 * std::ceil(mean_all)));
+  long long sn = 0;
+  long long scount = 0;
+  for (int r = 0; r < nrows; ++r) {
+    const int len = rp[r + 1] - rp[r];
+    if (len <= S.long_thresh) {
+      sn += len;
+      ++scount;
+    } else {
+      S.long_rows.push_back(r);
+      for (int b = rp[r]; b < rp[r + 1]; b += kChunk)
+        S.chunks.push_back(make_int4(r, b, std::min(b + kChunk, rp[r + 1]), b == rp[r] ? 1 : 0));
+    }
+  }
+  const double ms = scount ? (double)sn / (double)scount : 1.0;
+  int G = 1;
+  while (G < 32 && (double)G < ms) G <<= 1;
+  S.group = G;
+  return S;
+}
+
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename V>
+  V* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    V* p = reinterpret_cast<V*>(base ? base + off : nullptr);
+    off += std::max<size_t>(count, 1) * sizeof(V);
+    return p;
+  }
+};
+
+Params make_params(const osqp_settings& s) {
+  Params P;
+  P.sigma = s.sigma;
+  P.alpha = s.alpha;
+  P.eps_abs = s.eps_abs;
+  P.eps_rel = s.eps_rel;
+  P.eps_pinf = s.eps_pinf;
+  P.eps_dinf = s.eps_dinf;
+  P.rho_tol = s.adaptive_rho_tolerance;
+  P.eps_equil = s.eps_equil;
+  P.pcg_kappa = s.pcg_tol_fraction;
+  P.pcg_floor = s.pcg_tol_floor;
+  // FP32 PCG can only shrink the residual by a few orders per ADMM
+  // iteration; the next iteration restarts from an FP64 residual.
+  P.pcg_reduce = s.precision == OSQP_PRECISION_FP32_MIXED ? 1e-5 : 0.0;
+  P.time_limit_ns = s.time_limit > 0 ? s.time_limit * 1e9 : 0.0;
+  P.max_iter = s.max_iter;
+  P.check_interval = s.check_interval;
+  P.adaptive_rho = s.adaptive_rho;
+  P.scaling_iters = s.scaling_iters;
+  P.max_rho_updates = s.max_rho_updates;
+  P.pcg_max_iter = s.pcg_max_iter;
+  P.barrier_timeout_ns = 2000000000ull;
+  return P;
+}
+
+bool valid_csc(const osqp_csc* M, int rows, int cols, bool upper) {
+  if (!M || M->n_rows != rows || M->n_cols != cols || M->nnz < 0) return false;
+  if (!M->colptr || (M->nnz > 0 && (!M->rowind || !M->val))) return false;
+  if (M->colptr[0] != 0 || M->colptr[cols] != M->nnz) return false;
+  for (int j = 0; j < cols; ++j) {
+    if (M->colptr[j + 1] < M->colptr[j]) return false;
+    for (int k = M->colptr[j]; k < M->colptr[j + 1]; ++k) {
+      const int i = M->rowind[k];
+      if (i < 0 || i >= rows) return false;
+      if (k > M->colptr[j] && i <= M->rowind[k - 1]) return false;
+      if (upper && i > j) return false;
+    }
+  }
+  return true;
+}
+
+bool finite_all(const double* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+int check_settings(const osqp_settings& s) {
+  if (!(s.rho > 0) || !(s.sigma > 0) || !(s.alpha > 0 && s.alpha < 2)) return OSQP_ERR_SETTINGS;
+  if (!(s.eps_abs >= 0) || !(s.eps_rel >= 0) || !(s.eps_pinf > 0) || !(s.eps_dinf > 0))
+    return OSQP_ERR_SETTINGS;
+  if (!(s.adaptive_rho_tolerance >= 1) || !(s.eps_equil >= 0) || !(s.pcg_tol_fraction >= 0) ||
+      !(s.pcg_tol_floor >= 0) || !(s.time_limit >= 0))
+    return OSQP_ERR_SETTINGS;
+  if (s.max_iter < 0 || s.check_interval < 1 || s.scaling_iters < 0 || s.max_rho_updates < 0 ||
+      s.pcg_max_iter < 1)
+    return OSQP_ERR_SETTINGS;
+  if (s.precision != OSQP_PRECISION_FP64 && s.precision != OSQP_PRECISION_FP32_MIXED)
+    return OSQP_ERR_SETTINGS;
+  if (s.launch < 0 || s.launch > 2) return OSQP_ERR_SETTINGS;
+  return OSQP_OK;
+}
+
+}  // namespace
+
+struct osqp_solver {
+  int device = 0, num_sms = 0, grid = 0, use_grid = 0;
+  cudaStream_t stream = nullptr;
+  osqp_settings set{};
+  Params P{};
+  int n = 0, m = 0, nnzP = 0, nnzA = 0, nnzKn = 0;
+  std::vector<int> kn_rp, kn_ci, kn_src, a_rp, a_ci, a_src;
+  SchedHost kn_s, a_s;
+  char* arena = nullptr;
+  Dev<double> d64{};
+  Dev<float> d32{};
+  double* raw_in = nullptr;
+  int *kn_src_d = nullptr, *a_src_d = nullptr;
+  double *x_ws = nullptr, *y_ws = nullptr;
+  Barrier* bar = nullptr;
+  int* err = nullptr;
+  double* part = nullptr;
+  Scalars* sc = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  osqp_info info{};
+  double rho_bar = 0.1;
+  bool solved = false;
+};
+
+namespace {
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) {                      \
+      if (e_ == cudaErrorMemoryAllocation) {      \
+        cudaGetLastError();                       \
+        return OSQP_ERR_OOM;                      \
+      }                                           \
+      return OSQP_ERR_CUDA;                       \
+    }                                             \
+  } while (0)
+
+template <typename T>
+void fill_dev(osqp_solver* s, Arena& A, Dev<T>& d, int4** kn_ch, int** kn_lr, int4** a_ch,
+              int** a_lr) {
+  const int n = s->n, m = s->m;
+  d.n = n;
+  d.m = m;
+  d.kn_rp = A.take<int>(n + 1);
+  d.kn_ci = A.take<int>(s->nnzKn);
+  d.kn_v = A.take<T>(s->nnzKn);
+  d.kn_raw = A.take<double>(s->nnzKn);
+  d.a_rp = A.take<int>(m + 1);
+  d.a_ci = A.take<int>(s->nnzA);
+  d.a_v = A.take<T>(s->nnzA);
+  d.a_raw = A.take<double>(s->nnzA);
+  *kn_ch = A.take<int4>(s->kn_s.chunks.size());
+  *kn_lr = A.take<int>(s->kn_s.long_rows.size());
+  *a_ch = A.take<int4>(s->a_s.chunks.size());
+  *a_lr = A.take<int>(s->a_s.long_rows.size());
+  d.q_raw = A.take<double>(n);
+  d.l_raw = A.take<double>(m);
+  d.u_raw = A.take<double>(m);
+  d.rtype = A.take<uint8_t>(m);
+  double** nvec[] = {&d.D, &d.q, &d.pdiag, &d.dg, &d.nrm_n, &d.x, &d.dx, &d.px,
+                     &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt};
+  for (double** p : nvec) *p = A.take<double>(n);
+  double** mvec[] = {&d.E, &d.l, &d.u, &d.rho, &d.rho_inv, &d.nrm_m, &d.z, &d.y,
+                     &d.dy, &d.ax, &d.adx, &d.azt, &d.z_out, &d.y_out, &d.pcert,
+                     &d.zt, &d.wm, &d.um};
+  for (double** p : mvec) *p = A.take<double>(m);
+  T** tn[] = {&d.dinv, &d.r, &d.b, &d.s, &d.p0, &d.p1, &d.Kp};
+  for (T** p : tn) *p = A.take<T>(n);
+  d.rt = A.take<T>(m);
+  d.kn.nrows = n;
+  d.kn.group = s->kn_s.group;
+  d.kn.long_thresh = s->kn_s.long_thresh;
+  d.kn.nchunks = (int)s->kn_s.chunks.size();
+  d.kn.nlong = (int)s->kn_s.long_rows.size();
+  d.kn.chunks = *kn_ch;
+  d.kn.long_rows = *kn_lr;
+  d.as.nrows = m;
+  d.as.group = s->a_s.group;
+  d.as.long_thresh = s->a_s.long_thresh;
+  d.as.nchunks = (int)s->a_s.chunks.size();
+  d.as.nlong = (int)s->a_s.long_rows.size();
+  d.as.chunks = *a_ch;
+  d.as.long_rows = *a_lr;
+}
+
+template <typename T>
+Dev<T>& dev_of(osqp_solver* s);
+template <>
+Dev<double>& dev_of<double>(osqp_solver* s) {
+  return s->d64;
+}
+template <>
+Dev<float>& dev_of<float>(osqp_solver* s) {
+  return s->d32;
+}
+
+template <typename T>
+int launch_scale(osqp_solver* s, int reset) {
+  Dev<T>& d = dev_of<T>(s);
+  if (s->use_grid) {
+    CK(cudaMemsetAsync(s->bar, 0, sizeof(Barrier), s->stream));
+    CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    double rb = s->rho_bar;
+    void* args[] = {(void*)&d, (void*)&s->P, (void*)&s->bar, (void*)&s->err, (void*)&s->part,
+                    (void*)&rb, (void*)&reset};
+    CK(cudaLaunchCooperativeKernel((const void*)k_scale_grid<T>, dim3(s->grid), dim3(kThreads), args,
+                                   0, s->stream));
+  } else {
+    k_scale_block<T><<<1, kThreads, 0, s->stream>>>(d, s->P, s->rho_bar, reset);
+    CK(cudaGetLastError());
+  }
+  return OSQP_OK;
+}
+
+template <typename T>
+int launch_refresh(osqp_solver* s) {
+  Dev<T>& d = dev_of<T>(s);
+  if (s->use_grid) {
+    CK(cudaMemsetAsync(s->bar, 0, sizeof(Barrier), s->stream));
+    CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    double rb = s->rho_bar;
+    void* args[] = {(void*)&d, (void*)&s->P, (void*)&s->bar, (void*)&s->err, (void*)&s->part,
+                    (void*)&rb};
+    CK(cudaLaunchCooperativeKernel((const void*)k_refresh_grid<T>, dim3(s->grid), dim3(kThreads),
+                                   args, 0, s->stream));
+  } else {
+    k_refresh_block<T><<<1, kThreads, 0, s->stream>>>(d, s->P, s->rho_bar);
+    CK(cudaGetLastError());
+  }
+  return OSQP_OK;
+}
+
+template <typename T>
+int launch_admm(osqp_solver* s) {
+  Dev<T>& d = dev_of<T>(s);
+  if (!s->set.warm_start) {
+    k_zero_iterates<T><<<64, 256, 0, s->stream>>>(d);
+    CK(cudaGetLastError());
+  }
+  if (s->use_grid) {
+    CK(cudaMemsetAsync(s->bar, 0, sizeof(Barrier), s->stream));
+    CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    void* args[] = {(void*)&d, (void*)&s->P, (void*)&s->bar, (void*)&s->err, (void*)&s->part};
+    CK(cudaLaunchCooperativeKernel((const void*)k_admm_grid<T>, dim3(s->grid), dim3(kThreads), args,
+                                   0, s->stream));
+  } else {
+    k_admm_block<T><<<1, kThreads, 0, s->stream>>>(d, s->P);
+    CK(cudaGetLastError());
+  }
+  return OSQP_OK;
+}
+
+template <typename T>
+int launch_warm(osqp_solver* s, const double* xw, const double* yw) {
+  Dev<T>& d = dev_of<T>(s);
+  k_warm_xy<T><<<64, 256, 0, s->stream>>>(d, xw, yw);
+  CK(cudaGetLastError());
+  k_warm_z<T><<<std::max(1, std::min(1024, (s->m + 7) / 8)), 256, 0, s->stream>>>(d);
+  CK(cudaGetLastError());
+  return OSQP_OK;
+}
+
+int do_scale(osqp_solver* s, int reset) {
+  return s->set.precision == OSQP_PRECISION_FP64 ? launch_scale<double>(s, reset)
+                                                 : launch_scale<float>(s, reset);
+}
+int do_refresh(osqp_solver* s) {
+  return s->set.precision == OSQP_PRECISION_FP64 ? launch_refresh<double>(s)
+                                                 : launch_refresh<float>(s);
+}
+int do_admm(osqp_solver* s) {
+  return s->set.precision == OSQP_PRECISION_FP64 ? launch_admm<double>(s) : launch_admm<float>(s);
+}
+int do_warm(osqp_solver* s, const double* xw, const double* yw) {
+  return s->set.precision == OSQP_PRECISION_FP64 ? launch_warm<double>(s, xw, yw)
+                                                 : launch_warm<float>(s, xw, yw);
+}
+
+template <typename T>
+const Dev<T>& cdev(const osqp_solver* s) {
+  return dev_of<T>(const_cast<osqp_solver*>(s));
+}
+
+// The double-precision arrays shared by both precisions are at the same
+// places in d64 and d32; read them through whichever is live.
+const double* out_x(const osqp_solver* s) {
+  return s->set.precision == OSQP_PRECISION_FP64 ? s->d64.x_out : s->d32.x_out;
+}
+const double* out_y(const osqp_solver* s) {
+  return s->set.precision == OSQP_PRECISION_FP64 ? s->d64.y_out : s->d32.y_out;
+}
+const double* out_z(const osqp_solver* s) {
+  return s->set.precision == OSQP_PRECISION_FP64 ? s->d64.z_out : s->d32.z_out;
+}
+const double* out_pc(const osqp_solver* s) {
+  return s->set.precision == OSQP_PRECISION_FP64 ? s->d64.pcert : s->d32.pcert;
+}
+const double* out_dc(const osqp_solver* s) {
+  return s->set.precision == OSQP_PRECISION_FP64 ? s->d64.dcert : s->d32.dcert;
+}
+
+template <typename T>
+void raw_ptrs(osqp_solver* s, double** kn_raw, double** a_raw, double** q, double** l, double** u) {
+  Dev<T>& d = dev_of<T>(s);
+  *kn_raw = const_cast<double*>(d.kn_raw);
+  *a_raw = const_cast<double*>(d.a_raw);
+  *q = const_cast<double*>(d.q_raw);
+  *l = const_cast<double*>(d.l_raw);
+  *u = const_cast<double*>(d.u_raw);
+}
+
+void get_raw(osqp_solver* s, double** kn_raw, double** a_raw, double** q, double** l, double** u) {
+  if (s->set.precision == OSQP_PRECISION_FP64) raw_ptrs<double>(s, kn_raw, a_raw, q, l, u);
+  else raw_ptrs<float>(s, kn_raw, a_raw, q, l, u);
+}
+
+// Values of raw_in (CSC order: P upper then A) → CSR orders of Kn and Ā.
+int scatter_raw(osqp_solver* s) {
+  double *kn_raw, *a_raw, *q, *l, *u;
+  get_raw(s, &kn_raw, &a_raw, &q, &l, &u);
+  if (s->nnzKn > 0) {
+    k_gather<<<std::min(4096, (s->nnzKn + 255) / 256), 256, 0, s->stream>>>(kn_raw, s->kn_src_d,
+                                                                             s->raw_in, s->nnzKn);
+    CK(cudaGetLastError());
+  }
+  if (s->nnzA > 0) {
+    k_gather<<<std::min(4096, (s->nnzA + 255) / 256), 256, 0, s->stream>>>(a_raw, s->a_src_d,
+                                                                           s->raw_in, s->nnzA);
+    CK(cudaGetLastError());
+  }
+  return OSQP_OK;
+}
+
+int read_scalars(osqp_solver* s, Scalars* out) {
+  CK(cudaMemcpyAsync(out, s->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return OSQP_OK;
+}
+
+int check_device_error(osqp_solver* s) {
+  if (!s->use_grid) return OSQP_OK;
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return e == kDevOk ? OSQP_OK : OSQP_ERR_DEVICE;
+}
+
+int build_structure(osqp_solver* s, const osqp_csc* P, const osqp_csc* A) {
+  const int n = s->n, m = s->m;
+  // Full symmetric P rows (row j of P̄ = column j), each entry → index in P_upper.
+  std::vector<std::vector<std::pair<int, int>>> prow(n);
+  for (int j = 0; j < n; ++j)
+    for (int k = P->colptr[j]; k < P->colptr[j + 1]; ++k) {
+      const int i = P->rowind[k];
+      prow[j].push_back({i, k});
+      if (i != j) prow[i].push_back({j, k});
+    }
+  s->kn_rp.assign(n + 1, 0);
+  for (int j = 0; j < n; ++j) {
+    std::sort(prow[j].begin(), prow[j].end());
+    s->kn_rp[j + 1] = s->kn_rp[j] + (int)prow[j].size() + (A->colptr[j + 1] - A->colptr[j]);
+  }
+  s->nnzKn = s->kn_rp[n];
+  s->kn_ci.resize(s->nnzKn);
+  s->kn_src.resize(s->nnzKn);
+  for (int j = 0; j < n; ++j) {
+    int pos = s->kn_rp[j];
+    for (auto& e : prow[j]) {
+      s->kn_ci[pos] = e.first;
+      s->kn_src[pos] = e.second;
+      ++pos;
+    }
+    for (int k = A->colptr[j]; k < A->colptr[j + 1]; ++k) {
+      s->kn_ci[pos] = n + A->rowind[k];
+      s->kn_src[pos] = s->nnzP + k;
+      ++pos;
+    }
+  }
+  // Ā in CSR by a counting sort of the CSC entries.
+  s->a_rp.assign(m + 1, 0);
+  for (int k = 0; k < s->nnzA; ++k) s->a_rp[A->rowind[k] + 1]++;
+  for (int i = 0; i < m; ++i) s->a_rp[i + 1] += s->a_rp[i];
+  s->a_ci.resize(s->nnzA);
+  s->a_src.resize(s->nnzA);
+  std::vector<int> next(s->a_rp.begin(), s->a_rp.end() - 1);
+  for (int j = 0; j < n; ++j)
+    for (int k = A->colptr[j]; k < A->colptr[j + 1]; ++k) {
+      const int d = next[A->rowind[k]]++;
+      s->a_ci[d] = j;
+      s->a_src[d] = s->nnzP + k;
+    }
+  s->kn_s = make_sched(s->kn_rp);
+  s->a_s = make_sched(s->a_rp);
+  return OSQP_OK;
+}
+
+template <typename T>
+size_t arena_bytes_for(osqp_solver* s, size_t part_doubles) {
+  Arena A;
+  Dev<T> d{};
+  int4 *a, *c;
+  int *b, *e;
+  fill_dev<T>(s, A, d, &a, &b, &c, &e);
+  A.take<double>(s->nnzP + s->nnzA);  // raw_in
+  A.take<int>(s->nnzKn);
+  A.take<int>(s->nnzA);
+  A.take<double>(s->n);
+  A.take<double>(s->m);
+  A.take<Barrier>(1);
+  A.take<int>(1);
+  A.take<double>(part_doubles);
+  A.take<Scalars>(1);
+  return A.off + 256;
+}
+
+template <typename T>
+int carve_and_upload(osqp_solver* s, size_t part_doubles) {
+  Arena A{s->arena, 0};
+  Dev<T>& d = dev_of<T>(s);
+  int4 *kn_ch, *a_ch;
+  int *kn_lr, *a_lr;
+  fill_dev<T>(s, A, d, &kn_ch, &kn_lr, &a_ch, &a_lr);
+  s->raw_in = A.take<double>(s->nnzP + s->nnzA);
+  s->kn_src_d = A.take<int>(s->nnzKn);
+  s->a_src_d = A.take<int>(s->nnzA);
+  s->x_ws = A.take<double>(s->n);
+  s->y_ws = A.take<double>(s->m);
+  s->bar = A.take<Barrier>(1);
+  s->err = A.take<int>(1);
+  s->part = A.take<double>(part_doubles);
+  s->sc = A.take<Scalars>(1);
+  d.sc = s->sc;
+  auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
+  };
+  CK(up((void*)d.kn_rp, s->kn_rp.data(), s->kn_rp.size() * sizeof(int)));
+  CK(up((void*)d.kn_ci, s->kn_ci.data(), s->kn_ci.size() * sizeof(int)));
+  CK(up((void*)d.a_rp, s->a_rp.data(), s->a_rp.size() * sizeof(int)));
+  CK(up((void*)d.a_ci, s->a_ci.data(), s->a_ci.size() * sizeof(int)));
+  CK(up(s->kn_src_d, s->kn_src.data(), s->kn_src.size() * sizeof(int)));
+  CK(up(s->a_src_d, s->a_src.data(), s->a_src.size() * sizeof(int)));
+  CK(up(kn_ch, s->kn_s.chunks.data(), s->kn_s.chunks.size() * sizeof(int4)));
+  CK(up(kn_lr, s->kn_s.long_rows.data(), s->kn_s.long_rows.size() * sizeof(int)));
+  CK(up(a_ch, s->a_s.chunks.data(), s->a_s.chunks.size() * sizeof(int4)));
+  CK(up(a_lr, s->a_s.long_rows.data(), s->a_s.long_rows.size() * sizeof(int)));
+  CK(cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->stream));
+  return OSQP_OK;
+}
+
+int upload_vectors(osqp_solver* s, const double* q, const double* l, const double* u,
+                   cudaMemcpyKind kind) {
+  double *kn_raw, *a_raw, *qd, *ld, *ud;
+  get_raw(s, &kn_raw, &a_raw, &qd, &ld, &ud);
+  if (q) CK(cudaMemcpyAsync(qd, q, sizeof(double) * s->n, kind, s->stream));
+  if (l && s->m) CK(cudaMemcpyAsync(ld, l, sizeof(double) * s->m, kind, s->stream));
+  if (u && s->m) CK(cudaMemcpyAsync(ud, u, sizeof(double) * s->m, kind, s->stream));
+  return OSQP_OK;
+}
+
+float elapsed_s(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
+  return ms * 1e-3f;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void osqp_set_default_settings(osqp_settings* s) {
+  if (!s) return;
+  std::memset(s, 0, sizeof(*s));
+  s->rho = 0.1;
+  s->sigma = 1e-6;
+  s->alpha = 1.6;
+  s->eps_abs = 1e-3;
+  s->eps_rel = 1e-3;
+  s->eps_pinf = 1e-4;
+  s->eps_dinf = 1e-4;
+  s->adaptive_rho_tolerance = 5.0;
+  s->eps_equil = 1e-3;
+  s->pcg_tol_fraction = 0.15;
+  s->pcg_tol_floor = 1e-10;
+  s->time_limit = 0.0;
+  s->max_iter = 4000;
+  s->check_interval = 25;
+  s->adaptive_rho = 1;
+  s->scaling_iters = 10;
+  s->max_rho_updates = 20;
+  s->pcg_max_iter = 100;
+  s->precision = OSQP_PRECISION_FP64;
+  s->warm_start = 1;
+  s->launch = 0;
+}
+
+const char* osqp_error_message(int32_t code) {
+  switch (code) {
+    case OSQP_OK: return "ok";
+    case OSQP_ERR_DIMS: return "invalid dimensions";
+    case OSQP_ERR_CSC: return "invalid CSC matrix (pointers, ordering, range or triangle)";
+    case OSQP_ERR_NONFINITE: return "non-finite value in P, A or q, or NaN bound";
+    case OSQP_ERR_LGTU: return "lower bound greater than upper bound";
+    case OSQP_ERR_SETTINGS: return "invalid settings";
+    case OSQP_ERR_CUDA: return "CUDA runtime error";
+    case OSQP_ERR_OOM: return "device memory allocation failed";
+    case OSQP_ERR_ARG: return "NULL solver or required argument";
+    case OSQP_ERR_DEVICE: return "device-side wait timed out";
+    case OSQP_ERR_LIMIT: return "problem size beyond this entry point's limit";
+    default: return "unknown code";
+  }
+}
+
+int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const osqp_csc* A,
+                   const double* l, const double* u, const osqp_settings* settings,
+                   void* stream) {
+  if (!out || !P || !A || !q || !settings) return OSQP_ERR_ARG;
+  *out = nullptr;
+  const int n = P->n_cols, m = A->n_rows;
+  if (n < 1 || m < 0 || P->n_rows != n || A->n_cols != n) return OSQP_ERR_DIMS;
+  if (m > 0 && (!l || !u)) return OSQP_ERR_ARG;
+  if (!valid_csc(P, n, n, true) || !valid_csc(A, m, n, false)) return OSQP_ERR_CSC;
+  if (!finite_all(P->val, P->nnz) || !finite_all(A->val, A->nnz) || !finite_all(q, n))
+    return OSQP_ERR_NONFINITE;
+  for (int i = 0; i < m; ++i) {
+    if (std::isnan(l[i]) || std::isnan(u[i])) return OSQP_ERR_NONFINITE;
+    if (l[i] > u[i]) return OSQP_ERR_LGTU;
+  }
+  int rc = check_settings(*settings);
+  if (rc) return rc;
+
+  osqp_solver* s = new (std::nothrow) osqp_solver();
+  if (!s) return OSQP_ERR_OOM;
+  s->set = *settings;
+  s->P = make_params(*settings);
+  s->stream = (cudaStream_t)stream;
+  s->n = n;
+  s->m = m;
+  s->nnzP = P->nnz;
+  s->nnzA = A->nnz;
+  s->rho_bar = settings->rho;
+  auto fail = [&](int code) {
+    osqp_cleanup(s);
+    return code;
+  };
+  if (cudaGetDevice(&s->device) != cudaSuccess) return fail(OSQP_ERR_CUDA);
+  if (cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
+    return fail(OSQP_ERR_CUDA);
+  build_structure(s, P, A);
+
+  // Launch shape: one persistent CTA for small problems, else a cooperative
+  // grid of every SM slot the kernel can hold.
+  const long long work = (long long)s->nnzKn + s->nnzA + n + m;
+  s->use_grid = settings->launch == 2 || (settings->launch == 0 && work > 60000);
+  int per_sm = 1;
+  {
+    int occ = 0;
+    cudaError_t e = settings->precision == OSQP_PRECISION_FP64
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_admm_grid<double>,
+                                                                        kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_admm_grid<float>,
+                                                                        kThreads, 0);
+    if (e != cudaSuccess) return fail(OSQP_ERR_CUDA);
+    int occ2 = 0;
+    e = settings->precision == OSQP_PRECISION_FP64
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_scale_grid<double>, kThreads, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_scale_grid<float>, kThreads, 0);
+    if (e != cudaSuccess) return fail(OSQP_ERR_CUDA);
+    int occ3 = 0;
+    e = settings->precision == OSQP_PRECISION_FP64
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_refresh_grid<double>, kThreads,
+                                                            0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_refresh_grid<float>, kThreads,
+                                                            0);
+    if (e != cudaSuccess) return fail(OSQP_ERR_CUDA);
+    per_sm = std::max(1, std::min(std::min(occ, occ2), std::min(occ3, 2)));
+  }
+  s->grid = s->num_sms * per_sm;
+  const size_t part_doubles = (size_t)2 * s->grid * kMaxRed;
+  const size_t bytes = settings->precision == OSQP_PRECISION_FP64
+                           ? arena_bytes_for<double>(s, part_doubles)
+                           : arena_bytes_for<float>(s, part_doubles);
+  cudaError_t e = cudaMalloc((void**)&s->arena, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s->arena = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? OSQP_ERR_OOM : OSQP_ERR_CUDA);
+  }
+  for (auto& ev : s->ev)
+    if (cudaEventCreate(&ev) != cudaSuccess) return fail(OSQP_ERR_CUDA);
+  rc = settings->precision == OSQP_PRECISION_FP64 ? carve_and_upload<double>(s, part_doubles)
+                                                  : carve_and_upload<float>(s, part_doubles);
+  if (rc) return fail(rc);
+  if (s->nnzP && cudaMemcpyAsync(s->raw_in, P->val, sizeof(double) * s->nnzP,
+                                 cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+    return fail(OSQP_ERR_CUDA);
+  if (s->nnzA && cudaMemcpyAsync(s->raw_in + s->nnzP, A->val, sizeof(double) * s->nnzA,
+                                 cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+    return fail(OSQP_ERR_CUDA);
+  if ((rc = upload_vectors(s, q, l, u, cudaMemcpyHostToDevice))) return fail(rc);
+  if ((rc = scatter_raw(s))) return fail(rc);
+  if (cudaEventRecord(s->ev[0], s->stream) != cudaSuccess) return fail(OSQP_ERR_CUDA);
+  if ((rc = do_scale(s, 1))) return fail(rc);
+  if (cudaEventRecord(s->ev[1], s->stream) != cudaSuccess) return fail(OSQP_ERR_CUDA);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(OSQP_ERR_CUDA);
+  if ((rc = check_device_error(s))) return fail(rc);
+  s->info.setup_time = elapsed_s(s->ev[0], s->ev[1]);
+  s->info.launch = s->use_grid ? 2 : 1;
+  *out = s;
+  return OSQP_OK;
+}
+
+int32_t osqp_solve_async(osqp_solver* s) {
+  if (!s) return OSQP_ERR_ARG;
+  CK(cudaEventRecord(s->ev[2], s->stream));
+  int rc = do_admm(s);
+  if (rc) return rc;
+  CK(cudaEventRecord(s->ev[3], s->stream));
+  s->solved = true;
+  return OSQP_OK;
+}
+
+static int32_t refresh_info(osqp_solver* s) {
+  Scalars sc;
+  int rc;
+  if ((rc = read_scalars(s, &sc))) return rc;
+  if ((rc = check_device_error(s))) return rc;
+  s->info.status = sc.status;
+  s->info.iter = sc.iter;
+  s->info.pcg_iters = sc.pcg_iters;
+  s->info.rho_updates = sc.rho_updates;
+  s->info.ruiz_passes = sc.ruiz_passes;
+  s->info.obj_val = sc.obj;
+  s->info.prim_res = sc.prim_res;
+  s->info.dual_res = sc.dual_res;
+  s->info.rho_estimate = sc.rho_bar;
+  s->info.solve_time = s->solved ? elapsed_s(s->ev[2], s->ev[3]) : 0.0;
+  s->rho_bar = sc.rho_bar;
+  return OSQP_OK;
+}
+
+int32_t osqp_solve(osqp_solver* s) {
+  if (!s) return OSQP_ERR_ARG;
+  int rc = osqp_solve_async(s);
+  if (rc) return rc;
+  return refresh_info(s);
+}
+
+int32_t osqp_update_vectors(osqp_solver* s, const double* q, const double* l, const double* u) {
+  if (!s) return OSQP_ERR_ARG;
+  if (q && !finite_all(q, s->n)) return OSQP_ERR_NONFINITE;
+  // Check l ≤ u against the stored value of whichever side is not replaced.
+  if (l || u) {
+    std::vector<double> lh(s->m), uh(s->m);
+    double *kn_raw, *a_raw, *qd, *ld, *ud;
+    get_raw(s, &kn_raw, &a_raw, &qd, &ld, &ud);
+    if (!l && s->m) CK(cudaMemcpyAsync(lh.data(), ld, sizeof(double) * s->m, cudaMemcpyDeviceToHost, s->stream));
+    if (!u && s->m) CK(cudaMemcpyAsync(uh.data(), ud, sizeof(double) * s->m, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    const double* L = l ? l : lh.data();
+    const double* U = u ? u : uh.data();
+    for (int i = 0; i < s->m; ++i) {
+      if (std::isnan(L[i]) || std::isnan(U[i])) return OSQP_ERR_NONFINITE;
+      if (L[i] > U[i]) return OSQP_ERR_LGTU;
+    }
+  }
+  int rc = upload_vectors(s, q, l, u, cudaMemcpyHostToDevice);
+  if (rc) return rc;
+  if ((rc = do_refresh(s))) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  return check_device_error(s);
+}
+
+int32_t osqp_update_matrices(osqp_solver* s, const double* Pv, const double* Av) {
+  if (!s) return OSQP_ERR_ARG;
+  if (Pv && !finite_all(Pv, s->nnzP)) return OSQP_ERR_NONFINITE;
+  if (Av && !finite_all(Av, s->nnzA)) return OSQP_ERR_NONFINITE;
+  if (Pv && s->nnzP)
+    CK(cudaMemcpyAsync(s->raw_in, Pv, sizeof(double) * s->nnzP, cudaMemcpyHostToDevice, s->stream));
+  if (Av && s->nnzA)
+    CK(cudaMemcpyAsync(s->raw_in + s->nnzP, Av, sizeof(double) * s->nnzA, cudaMemcpyHostToDevice,
+                       s->stream));
+  int rc = scatter_raw(s);
+  if (rc) return rc;
+  CK(cudaEventRecord(s->ev[0], s->stream));
+  if ((rc = do_scale(s, 0))) return rc;
+  CK(cudaEventRecord(s->ev[1], s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->info.setup_time = elapsed_s(s->ev[0], s->ev[1]);
+  return check_device_error(s);
+}
+
+static int32_t load_data(osqp_solver* s, const double* Pv, const double* q, const double* Av,
+                         const double* l, const double* u, cudaMemcpyKind kind) {
+  if (!s || !q || (s->nnzP && !Pv) || (s->nnzA && !Av) || (s->m && (!l || !u)))
+    return OSQP_ERR_ARG;
+  if (s->nnzP) CK(cudaMemcpyAsync(s->raw_in, Pv, sizeof(double) * s->nnzP, kind, s->stream));
+  if (s->nnzA)
+    CK(cudaMemcpyAsync(s->raw_in + s->nnzP, Av, sizeof(double) * s->nnzA, kind, s->stream));
+  int rc = upload_vectors(s, q, l, u, kind);
+  if (rc) return rc;
+  if ((rc = scatter_raw(s))) return rc;
+  s->rho_bar = s->set.rho;
+  return do_scale(s, 1);
+}
+
+int32_t osqp_load_data(osqp_solver* s, const double* Pv, const double* q, const double* Av,
+                       const double* l, const double* u) {
+  return load_data(s, Pv, q, Av, l, u, cudaMemcpyHostToDevice);
+}
+
+int32_t osqp_load_data_device(osqp_solver* s, const double* Pv, const double* q, const double* Av,
+                              const double* l, const double* u) {
+  return load_data(s, Pv, q, Av, l, u, cudaMemcpyDeviceToDevice);
+}
+
+int32_t osqp_update_rho(osqp_solver* s, double rho_bar) {
+  if (!s) return OSQP_ERR_ARG;
+  if (!(rho_bar > 0) || !std::isfinite(rho_bar)) return OSQP_ERR_SETTINGS;
+  s->rho_bar = rho_bar;
+  int rc = do_refresh(s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  return check_device_error(s);
+}
+
+int32_t osqp_warm_start(osqp_solver* s, const double* x, const double* y) {
+  if (!s) return OSQP_ERR_ARG;
+  if (x && !finite_all(x, s->n)) return OSQP_ERR_NONFINITE;
+  if (y && !finite_all(y, s->m)) return OSQP_ERR_NONFINITE;
+  if (x) CK(cudaMemcpyAsync(s->x_ws, x, sizeof(double) * s->n, cudaMemcpyHostToDevice, s->stream));
+  if (y && s->m)
+    CK(cudaMemcpyAsync(s->y_ws, y, sizeof(double) * s->m, cudaMemcpyHostToDevice, s->stream));
+  int rc = do_warm(s, x ? s->x_ws : nullptr, y ? s->y_ws : nullptr);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  return OSQP_OK;
+}
+
+int32_t osqp_get_solution(osqp_solver* s, double* x, double* y, double* z, osqp_info* info) {
+  if (!s) return OSQP_ERR_ARG;
+  if (x) CK(cudaMemcpyAsync(x, out_x(s), sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+  if (y && s->m)
+    CK(cudaMemcpyAsync(y, out_y(s), sizeof(double) * s->m, cudaMemcpyDeviceToHost, s->stream));
+  if (z && s->m)
+    CK(cudaMemcpyAsync(z, out_z(s), sizeof(double) * s->m, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (info) {
+    int rc = refresh_info(s);
+    if (rc) return rc;
+    *info = s->info;
+  }
+  return OSQP_OK;
+}
+
+int32_t osqp_get_solution_device(osqp_solver* s, double* x, double* y) {
+  if (!s) return OSQP_ERR_ARG;
+  if (x) CK(cudaMemcpyAsync(x, out_x(s), sizeof(double) * s->n, cudaMemcpyDeviceToDevice, s->stream));
+  if (y && s->m)
+    CK(cudaMemcpyAsync(y, out_y(s), sizeof(double) * s->m, cudaMemcpyDeviceToDevice, s->stream));
+  return OSQP_OK;
+}
+
+int32_t osqp_get_certificate(osqp_solver* s, double* py, double* dx) {
+  if (!s) return OSQP_ERR_ARG;
+  if (py && s->m)
+    CK(cudaMemcpyAsync(py, out_pc(s), sizeof(double) * s->m, cudaMemcpyDeviceToHost, s->stream));
+  if (dx) CK(cudaMemcpyAsync(dx, out_dc(s), sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return OSQP_OK;
+}
+
+int32_t osqp_cleanup(osqp_solver* s) {
+  if (!s) return OSQP_ERR_ARG;
+  int rc = OSQP_OK;
+  if (s->stream || s->arena) {
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) rc = OSQP_ERR_CUDA;
+  }
+  if (s->arena && cudaFree(s->arena) != cudaSuccess) rc = OSQP_ERR_CUDA;
+  for (auto& ev : s->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete s;
+  return rc;
+}
+
+}  // extern "C"

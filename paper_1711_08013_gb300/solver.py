@@ -1,0 +1,77 @@
+"""Convenience object over the C ABI (one solver = one QP resident on the GPU)."""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import _binding as B
+
+
+@dataclasses.dataclass
+class Result:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    status: int
+    iter: int
+    pcg_iters: int
+    rho_updates: int
+    obj_val: float
+    prim_res: float
+    dual_res: float
+    rho_estimate: float
+    setup_time: float
+    solve_time: float
+    launch: int
+
+
+class Solver:
+    """``Solver(qp, **settings)`` with ``qp`` exposing P (upper CSC), q, A, l, u."""
+
+    def __init__(self, qp, stream: int | None = None, **settings):
+        self.n, self.m = qp.P.shape[0], qp.A.shape[0]
+        self.settings = B.osqp_set_default_settings(**settings)
+        self.handle = B.osqp_setup(qp.P, qp.q, qp.A, qp.l, qp.u, self.settings, stream)
+
+    def solve(self) -> Result:
+        B.osqp_solve(self.handle)
+        return self.result()
+
+    def result(self) -> Result:
+        x, y, z, info = B.osqp_get_solution(self.handle, self.n, self.m)
+        return Result(x, y, z, info.status, info.iter, info.pcg_iters, info.rho_updates,
+                      info.obj_val, info.prim_res, info.dual_res, info.rho_estimate,
+                      info.setup_time, info.solve_time, info.launch)
+
+    def certificate(self):
+        return B.osqp_get_certificate(self.handle, self.n, self.m)
+
+    def update_vectors(self, q=None, l=None, u=None):
+        B.osqp_update_vectors(self.handle, q, l, u)
+
+    def update_matrices(self, P_val=None, A_val=None):
+        B.osqp_update_matrices(self.handle, P_val, A_val)
+
+    def update_rho(self, rho_bar: float):
+        B.osqp_update_rho(self.handle, rho_bar)
+
+    def warm_start(self, x=None, y=None):
+        B.osqp_warm_start(self.handle, x, y)
+
+    def close(self):
+        if self.handle:
+            B.osqp_cleanup(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -59,3 +59,17 @@ def dual_cert_ok(qp, x, eps=1e-3):
     ok &= np.where(~uf & lf, Ax >= -eps * nx, True)
     ok &= np.where(~lf & uf, Ax <= eps * nx, True)
     return bool(np.all(ok))
+
+
+def objective_interval(qp, x, z, y, x_star, y_star):
+    """Bounds on f(x) − f* for a point with z ∈ C and y ∈ N_C(z) (true of
+    every ADMM iterate, §3.3), from convexity of f and the normal-cone
+    inequalities, with (x*, y*) an optimal primal-dual pair:
+        −‖y*‖₁‖r_p‖∞ ≤ f(x) − f* ≤ ‖r_d‖∞‖x − x*‖₁ + ‖y‖₁‖r_p‖∞,
+    r_p = Ax − z, r_d = Px + q + Aᵀy (Eqs. res_prim, res_dual)."""
+    P = full_P(qp)
+    rp = np.max(np.abs(qp.A @ x - z), initial=0.0)
+    rd = np.max(np.abs(P @ x + qp.q + qp.A.T @ y))
+    lo = -np.sum(np.abs(y_star)) * rp
+    hi = rd * np.sum(np.abs(x - x_star)) + np.sum(np.abs(y)) * rp
+    return lo, hi

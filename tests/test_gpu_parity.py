@@ -1,0 +1,234 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_1711_08013_gb300 import _binding as B
+from paper_1711_08013_gb300 import problems as pb
+from tests.kkt_check import acceptance, dual_cert_ok, objective, objective_interval, primal_cert_ok
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1711_08013_gb300.solver import Solver  # noqa: E402
+
+# Exact-solve settings for iterate parity: fixed ρ, no termination, PCG run
+# to a residual of 1e-14·‖rhs‖∞ so that the indirect and direct forms of §3.1
+# produce the same iterates.
+STEP_GPU = dict(adaptive_rho=0, eps_abs=0.0, eps_rel=0.0, eps_pinf=1e-300, eps_dinf=1e-300,
+                pcg_tol_fraction=0.0, pcg_tol_floor=1e-14, pcg_max_iter=2000, check_interval=1)
+STEP_ORACLE = dict(adaptive_rho=0, eps_abs=0.0, eps_rel=0.0, eps_pinf=1e-300, eps_dinf=1e-300,
+                   check_interval=1)
+HIGH_ORACLE = dict(eps_abs=1e-9, eps_rel=1e-9, max_iter=400000, check_interval=10)
+
+
+def small_classes():
+    return [
+        ("random_qp", pb.random_qp(30, 120, seed=3)),
+        ("eq_qp", pb.eq_qp(40, seed=2, density=0.3)),
+        ("mpc", pb.mpc(6, 8, seed=4)),
+        ("portfolio", pb.portfolio(3, seed=5)),   # 300-entry 1ᵀx row: long-row chunks
+        ("lasso", pb.lasso(6, seed=6)),
+        ("lasso_long", pb.lasso(2, seed=7, m=1500)),  # ~225-entry columns and longer
+        ("huber", pb.huber(5, seed=8)),
+        ("svm", pb.svm(5, seed=9)),
+        ("box", pb.box_qp(40, seed=10)),
+    ]
+
+
+CLASSES = small_classes()
+IDS = [c[0] for c in CLASSES]
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b), initial=0.0) / max(1.0, np.max(np.abs(b), initial=0.0))
+
+
+@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("iters", [1, 7, 40])
+@pytest.mark.parametrize("name,qp", CLASSES, ids=IDS)
+def test_step_parity_fp64(oracle_mod, name, qp, iters, launch):
+    """Iterates after k ADMM iterations (fixed ρ, exact linear solves) equal
+    the oracle's direct-method iterates (§3.1: both solve Eq. kkt)."""
+    o = oracle_mod.solve(qp, max_iter=iters, **STEP_ORACLE)
+    with Solver(qp, max_iter=iters, launch=launch, **STEP_GPU) as s:
+        g = s.solve()
+    assert g.iter == iters
+    assert rel_err(g.x, o.x) <= 1e-8, name
+    assert rel_err(g.z, o.z) <= 1e-8, name
+    assert rel_err(g.y, o.y) <= 1e-8, name
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("name,qp", CLASSES, ids=IDS)
+def test_end_to_end_eps_1e3(oracle_mod, name, qp, launch, precision):
+    """ε = 1e-3: both results pass the acceptance test of §8 and the GPU
+    objective lies in the convexity interval around the optimum."""
+    star = oracle_mod.solve(qp, **HIGH_ORACLE)
+    o = oracle_mod.solve(qp)
+    with Solver(qp, launch=launch, precision=precision) as s:
+        g = s.solve()
+    assert g.status == B.SOLVED, (name, g.status, g.iter)
+    assert o.status == oracle_mod.SOLVED
+    prim, dual, ep, ed = acceptance(qp, g.x, g.y, 1e-3, 1e-3)
+    assert prim <= ep * 1.01 and dual <= ed * 1.01, (name, prim, ep, dual, ed)
+    lo, hi = objective_interval(qp, g.x, g.z, g.y, star.x, star.y)
+    d = objective(qp, g.x) - star.obj_val
+    slack = 1e-7 * max(1.0, abs(star.obj_val))
+    assert lo - slack <= d <= hi + slack, (name, lo, d, hi)
+    assert abs(g.obj_val - objective(qp, g.x)) <= 1e-6 * max(1.0, abs(g.obj_val))
+    # z ∈ [l, u] and the sign pattern of y (§3.3) hold for the GPU result
+    assert np.all(g.z >= qp.l - 1e-12 * (1 + np.abs(qp.l))) and np.all(g.z <= qp.u + 1e-12 * (1 + np.abs(qp.u)))
+
+
+@pytest.mark.parametrize("name,qp", CLASSES, ids=IDS)
+def test_high_accuracy_objective(oracle_mod, name, qp):
+    """ε = 1e-6 (FP64): objective relative error against the oracle ≤ 1e-4."""
+    o = oracle_mod.solve(qp, eps_abs=1e-6, eps_rel=1e-6, max_iter=200000)
+    with Solver(qp, eps_abs=1e-6, eps_rel=1e-6, max_iter=200000) as s:
+        g = s.solve()
+    assert g.status == B.SOLVED and o.status == oracle_mod.SOLVED
+    assert abs(g.obj_val - o.obj_val) <= 1e-4 * max(1.0, abs(o.obj_val))
+    prim, dual, ep, ed = acceptance(qp, g.x, g.y, 1e-6, 1e-6)
+    assert prim <= ep * 1.01 and dual <= ed * 1.01
+
+
+@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("seed", range(3))
+def test_primal_infeasible(launch, seed):
+    qp = pb.primal_infeasible_qp(4, seed=seed)
+    with Solver(qp, launch=launch) as s:
+        g = s.solve()
+        py, _ = s.certificate()
+    assert g.status == B.PRIMAL_INFEASIBLE
+    assert primal_cert_ok(qp, py, eps=1e-3)
+
+
+@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("seed", range(3))
+def test_dual_infeasible(launch, seed):
+    qp = pb.dual_infeasible_lp(3 + seed, seed=seed)
+    with Solver(qp, launch=launch) as s:
+        g = s.solve()
+        _, dx = s.certificate()
+    assert g.status == B.DUAL_INFEASIBLE
+    assert dual_cert_ok(qp, dx, eps=1e-3)
+
+
+def _edge_cases():
+    rng = np.random.default_rng(0)
+    out = []
+    # m = 0: unconstrained, x = −P⁻¹q
+    P = sp.csc_matrix(np.diag([2.0, 3.0, 4.0]))
+    out.append(("m0", pb._finish("m0", P, np.array([1.0, -1.0, 2.0]), sp.csc_matrix((0, 3)),
+                                 np.zeros(0), np.zeros(0))))
+    # n = 1
+    out.append(("n1", pb._finish("n1", sp.csc_matrix([[1.0]]), np.array([-3.0]),
+                                 sp.csc_matrix([[1.0], [2.0]]), np.array([-1.0, -1.0]),
+                                 np.array([1.0, 1.0]))))
+    # empty rows and an empty column in A, one free row
+    A = pb.sprandn(rng, 12, 8, 0.4).toarray()
+    A[3, :] = 0.0
+    A[:, 5] = 0.0
+    l = -np.ones(12)
+    u = np.ones(12)
+    l[7], u[7] = -np.inf, np.inf
+    M = rng.standard_normal((8, 8))
+    out.append(("empty_rows", pb._finish("empty", sp.csc_matrix(M @ M.T + np.eye(8)),
+                                         rng.standard_normal(8), sp.csc_matrix(A), l, u)))
+    # feasible LP (P = 0) with boxes
+    A = pb.sprandn(rng, 20, 10, 0.3)
+    A = sp.vstack([sp.eye(10), A]).tocsc()
+    out.append(("lp", pb._finish("lp", sp.csc_matrix((10, 10)), rng.standard_normal(10), A,
+                                 np.concatenate([-np.ones(10), -5 * np.ones(20)]),
+                                 np.concatenate([np.ones(10), 5 * np.ones(20)]))))
+    return out
+
+
+EDGE = _edge_cases()
+
+
+@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("name,qp", EDGE, ids=[e[0] for e in EDGE])
+def test_edge_cases(oracle_mod, name, qp, launch):
+    star = oracle_mod.solve(qp, **HIGH_ORACLE)
+    with Solver(qp, launch=launch, eps_abs=1e-6, eps_rel=1e-6, max_iter=100000) as s:
+        g = s.solve()
+    assert g.status == B.SOLVED, (name, g.status)
+    assert abs(g.obj_val - star.obj_val) <= 1e-4 * max(1.0, abs(star.obj_val))
+    if name == "m0":
+        assert np.allclose(g.x, -np.array([1 / 2.0, -1 / 3.0, 2 / 4.0]), atol=1e-5)
+
+
+def test_update_vectors_and_warm_start(oracle_mod):
+    qp = pb.random_qp(40, 200, seed=12)
+    rng = np.random.default_rng(1)
+    with Solver(qp) as s:
+        first = s.solve()
+        assert first.status == B.SOLVED
+        q2, l2, u2 = pb.perturb_vectors(rng, qp)
+        s.update_vectors(q2, l2, u2)
+        g = s.solve()
+    qp2 = pb._finish("p", qp.P, q2, qp.A, l2, u2)
+    star = oracle_mod.solve(qp2, **HIGH_ORACLE)
+    assert g.status == B.SOLVED
+    prim, dual, ep, ed = acceptance(qp2, g.x, g.y, 1e-3, 1e-3)
+    assert prim <= ep * 1.01 and dual <= ed * 1.01
+    lo, hi = objective_interval(qp2, g.x, g.z, g.y, star.x, star.y)
+    assert lo - 1e-7 <= objective(qp2, g.x) - star.obj_val <= hi + 1e-7
+
+
+def test_warm_start_from_solution_terminates_at_first_check(oracle_mod):
+    qp = pb.random_qp(30, 150, seed=13)
+    star = oracle_mod.solve(qp, **HIGH_ORACLE)
+    with Solver(qp, check_interval=1) as s:
+        s.warm_start(star.x, star.y)
+        g = s.solve()
+    assert g.status == B.SOLVED and g.iter <= 2
+
+
+def test_update_matrices(oracle_mod):
+    qp = pb.random_qp(30, 120, seed=14)
+    rng = np.random.default_rng(2)
+    Pv = qp.P.data * (1.0 + 0.1 * rng.random(qp.P.nnz))
+    Av = qp.A.data + 0.1 * rng.standard_normal(qp.A.nnz)
+    with Solver(qp, eps_abs=1e-6, eps_rel=1e-6, max_iter=100000) as s:
+        s.solve()
+        s.update_matrices(Pv, Av)
+        g = s.solve()
+    qp2 = pb._finish("m", sp.csc_matrix((Pv, qp.P.indices, qp.P.indptr), shape=qp.P.shape), qp.q,
+                     sp.csc_matrix((Av, qp.A.indices, qp.A.indptr), shape=qp.A.shape), qp.l, qp.u)
+    o = oracle_mod.solve(qp2, eps_abs=1e-6, eps_rel=1e-6, max_iter=100000)
+    assert g.status == B.SOLVED
+    assert abs(g.obj_val - o.obj_val) <= 1e-4 * max(1.0, abs(o.obj_val))
+
+
+def test_update_rho_still_converges():
+    qp = pb.random_qp(30, 120, seed=15)
+    with Solver(qp, adaptive_rho=0) as s:
+        s.update_rho(3.0)
+        g = s.solve()
+    assert g.status == B.SOLVED and abs(g.rho_estimate - 3.0) < 1e-12
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("config", [0, 1, 2])
+def test_configs_full_size(oracle_mod, config, precision):
+    """The single-problem workloads at full size in the launch shape the
+    benchmark uses (automatic): acceptance at ε = 1e-3 and the objective
+    inside the convexity interval around the oracle's high-accuracy optimum."""
+    qp = pb.config_problem(config)
+    star = oracle_mod.solve(qp, eps_abs=1e-7, eps_rel=1e-7, max_iter=200000)
+    with Solver(qp, precision=precision) as s:
+        g = s.solve()
+    assert g.status == B.SOLVED, (config, g.status, g.iter)
+    prim, dual, ep, ed = acceptance(qp, g.x, g.y, 1e-3, 1e-3)
+    assert prim <= ep * 1.01 and dual <= ed * 1.01, (prim, ep, dual, ed)
+    lo, hi = objective_interval(qp, g.x, g.z, g.y, star.x, star.y)
+    d = objective(qp, g.x) - star.obj_val
+    slack = 1e-6 * max(1.0, abs(star.obj_val))
+    assert lo - slack <= d <= hi + slack, (lo, d, hi)
