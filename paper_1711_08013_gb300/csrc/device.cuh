@@ -154,6 +154,7 @@ struct GridTeam {
   double* sm;
   unsigned long long timeout_ns;
   int buf;
+  unsigned int target;  // barrier count × gridDim.x reached so far (thread 0)
 
   __device__ int nthreads() const { return gridDim.x * blockDim.x; }
   __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
@@ -161,34 +162,36 @@ struct GridTeam {
   __device__ int warp() const { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
   __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
 
-  // Grid barrier with a bounded wait: a CTA that waits longer than
-  // timeout_ns records kDevBarrierTimeout and leaves the barrier; every CTA
-  // then stops at its next check of the error word.
+  // Grid barrier with a bounded wait.  The arrival counter only grows
+  // during a launch (the host zeroes it before every launch), so barrier
+  // number k is complete once it reaches k·gridDim.x.  A CTA that waits
+  // longer than timeout_ns records kDevBarrierTimeout and leaves; every CTA
+  // stops at its next barrier.
   __device__ bool sync() {
     __syncthreads();
     if (threadIdx.x == 0) {
-      volatile unsigned int* vgen = &bar->gen;
-      const unsigned int g = *vgen;
+      target += gridDim.x;
       __threadfence();
-      const unsigned int arrived = atomicAdd(&bar->count, 1u);
-      if (arrived == gridDim.x - 1) {
-        atomicExch(&bar->count, 0u);
-        __threadfence();
-        atomicAdd(&bar->gen, 1u);
-      } else {
+      atomicAdd(&bar->count, 1u);
+      volatile unsigned int* vcount = &bar->count;
+      int ok = 1;
+      if (*vcount < target) {
         const unsigned long long t0 = gtimer();
         unsigned int spins = 0;
-        while (*vgen == g) {
+        while (*vcount < target) {
           if ((++spins & 255u) == 0 && gtimer() - t0 > timeout_ns) {
             atomicExch(err, kDevBarrierTimeout);
+            ok = 0;
             break;
           }
         }
       }
       __threadfence();
+      if (ok && *(volatile int*)err != kDevOk) ok = 0;
+      sm[34 * kMaxRed - 1] = ok ? 1.0 : 0.0;
     }
     __syncthreads();
-    return *(volatile int*)err == kDevOk;
+    return sm[34 * kMaxRed - 1] != 0.0;
   }
 
   template <int K>
@@ -269,8 +272,18 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* 
     if (e - b > S.long_thresh) continue;
     AT acc[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = MAXR ? AT(0) : AT(0);
-    for (int k = b + sub; k < e; k += Gw) gather(ci[k], va[k], acc);
+    for (int v = 0; v < NV; ++v) acc[v] = AT(0);
+    int k = b + sub;
+    // four nonzeros per lane per step: their loads are issued together
+    for (; k + 3 * Gw < e; k += 4 * Gw) {
+      const int c0 = ci[k], c1 = ci[k + Gw], c2 = ci[k + 2 * Gw], c3 = ci[k + 3 * Gw];
+      const MT v0 = va[k], v1 = va[k + Gw], v2 = va[k + 2 * Gw], v3 = va[k + 3 * Gw];
+      gather(c0, v0, acc);
+      gather(c1, v1, acc);
+      gather(c2, v2, acc);
+      gather(c3, v3, acc);
+    }
+    for (; k < e; k += Gw) gather(ci[k], va[k], acc);
     for (int off = Gw >> 1; off > 0; off >>= 1) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -285,7 +298,18 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* 
     AT acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = AT(0);
-    for (int k = ch.y + lane; k < ch.z; k += 32) gather(ci[k], va[k], acc);
+    // a chunk holds at most kChunk = 8·32 nonzeros: one batch of 8 per lane
+    int cc[kChunk / 32];
+    MT vv[kChunk / 32];
+#pragma unroll
+    for (int u = 0; u < kChunk / 32; ++u) {
+      const int k = ch.y + lane + 32 * u;
+      cc[u] = k < ch.z ? ci[k] : -1;
+      vv[u] = k < ch.z ? va[k] : MT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kChunk / 32; ++u)
+      if (cc[u] >= 0) gather(cc[u], vv[u], acc);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll

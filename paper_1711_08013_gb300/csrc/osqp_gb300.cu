@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kThreads) k_scale_grid(const __grid_constant__
                                                           Barrier* bar, int* err, double* part,
                                                           double rho_bar, int reset) {
   __shared__ double sm[kSmemDoubles];
-  GridTeam tm{bar, err, part, sm, P.barrier_timeout_ns, 0};
+  GridTeam tm{bar, err, part, sm, P.barrier_timeout_ns, 0, 0u};
   scale_stage(tm, d, P, rho_bar, reset != 0);
 }
 
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kThreads) k_refresh_grid(const __grid_constant
                                                             Barrier* bar, int* err, double* part,
                                                             double rho_bar) {
   __shared__ double sm[kSmemDoubles];
-  GridTeam tm{bar, err, part, sm, P.barrier_timeout_ns, 0};
+  GridTeam tm{bar, err, part, sm, P.barrier_timeout_ns, 0, 0u};
   refresh_stage(tm, d, P, rho_bar);
 }
 
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kThreads) k_admm_grid(const __grid_constant__ 
                                                          const __grid_constant__ Params P,
                                                          Barrier* bar, int* err, double* part) {
   __shared__ double sm[kSmemDoubles];
-  GridTeam tm{bar, err, part, sm, P.barrier_timeout_ns, 0};
+  GridTeam tm{bar, err, part, sm, P.barrier_timeout_ns, 0, 0u};
   admm_stage(tm, d, P);
 }
 
@@ -148,10 +148,23 @@ struct SchedHost {
   std::vector<int> long_rows;
 };
 
-// Row schedule from row-length statistics: rows longer than
-// max(256, 8·mean) are split into kChunk-nonzero chunks; the sub-warp width
-// is the smallest power of two ≥ the mean length of the remaining rows.
-SchedHost make_sched(const std::vector<int>& rp) {
+// Row schedule from row-length statistics.  Rows longer than
+// max(256, 8·mean) are split into kChunk-nonzero chunks handled by whole
+// warps.  The sub-warp width G for the other rows is the largest power of two
+// that still gives every group about one row (32·warps/rows), kept between
+// the width that caps a lane at 16 nonzeros of a mean row and the smallest
+// power of two ≥ the mean row length.
+int sched_group(double mean_short, long long nshort, long long nwarps) {
+  int g_mean = 1;
+  while (g_mean < 32 && (double)g_mean < mean_short) g_mean <<= 1;
+  int g_min = 1;
+  while (g_min < 32 && (double)g_min * 16.0 < mean_short) g_min <<= 1;
+  int g_occ = 1;
+  while (g_occ < 32 && (long long)(g_occ * 2) * nshort <= 32LL * nwarps) g_occ <<= 1;
+  return std::max(g_min, std::min(g_mean, g_occ));
+}
+
+SchedHost make_sched(const std::vector<int>& rp, long long nwarps) {
   SchedHost S;
   const int nrows = (int)rp.size() - 1;
   const long long nnz = nrows > 0 ? rp[nrows] : 0;
@@ -171,9 +184,7 @@ SchedHost make_sched(const std::vector<int>& rp) {
     }
   }
   const double ms = scount ? (double)sn / (double)scount : 1.0;
-  int G = 1;
-  while (G < 32 && (double)G < ms) G <<= 1;
-  S.group = G;
+  S.group = sched_group(ms, scount, nwarps);
   return S;
 }
 
@@ -547,8 +558,6 @@ int build_structure(osqp_solver* s, const osqp_csc* P, const osqp_csc* A) {
       s->a_ci[d] = j;
       s->a_src[d] = s->nnzP + k;
     }
-  s->kn_s = make_sched(s->kn_rp);
-  s->a_s = make_sched(s->a_rp);
   return OSQP_OK;
 }
 
@@ -737,6 +746,11 @@ int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const 
     per_sm = std::max(1, std::min(std::min(occ, occ2), std::min(occ3, 2)));
   }
   s->grid = s->num_sms * per_sm;
+  {
+    const long long nwarps = (long long)(s->use_grid ? s->grid : 1) * (kThreads / 32);
+    s->kn_s = make_sched(s->kn_rp, nwarps);
+    s->a_s = make_sched(s->a_rp, nwarps);
+  }
   const size_t part_doubles = (size_t)2 * s->grid * kMaxRed;
   const size_t bytes = settings->precision == OSQP_PRECISION_FP64
                            ? arena_bytes_for<double>(s, part_doubles)
