@@ -1,0 +1,501 @@
+// osqp_solve_noalloc: a whole small-QP solve that allocates no memory.
+//
+// Some callers cannot allocate device memory at solve time: code running
+// inside a CUDA-graph capture that must not touch the allocator, plugins
+// hosted by a framework that owns all device memory, or real-time loops that
+// forbid cudaMalloc/cudaFree after start-up.  For them this entry point runs
+// the same one-CTA solver as osqp_setup/osqp_solve with launch = 1 (Ruiz
+// scaling, ρ and Jacobi, Algorithm 1 with PCG, termination, unscaling), but
+// every intermediate array — including the CSR structure that osqp_setup
+// builds on the host — lives in one file-scope device array of
+// kNoallocScratchBytes.  The caller passes device inputs and outputs.
+//
+// The array is statically allocated in every GPU that loads the library and
+// stays there until the process exits.  Its device address is looked up once
+// per device (cudaGetSymbolAddress) by the first call made with that device
+// current; make that first call before any stream capture.  All calls share
+// the array: two calls whose kernels overlap on the GPU race on it, so
+// serialise them (one stream, or events).  The kernel clears every counter it
+// relies on at its start; the rest of the array keeps the last call's data.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/osqp_gb300.h"
+#include "../../include/osqp_gb300_noalloc.h"
+#include "device.cuh"
+
+using namespace osqpgb;
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = OSQP_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoallocMaxRow = 8192;  // rows longer than this are rejected (sort cost)
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+enum : int { kNaOk = 0, kNaBadCsc = 1, kNaLongRow = 2 };
+
+struct NaInput {
+  int n, m, nnzP, nnzA;
+  const int* Pp;
+  const int* Pi;
+  const double* Px;
+  const double* q;
+  const int* Ap;
+  const int* Ai;
+  const double* Ax;
+  const double* l;
+  const double* u;
+  double* x;
+  double* y;
+};
+
+// Scratch layout shared by the host size check and the device carve.
+template <typename T>
+struct NaLayout {
+  size_t total = 0;
+  template <typename V>
+  __host__ __device__ size_t take(size_t count) {
+    total = (total + 255) & ~(size_t)255;
+    size_t at = total;
+    total += (count ? count : 1) * sizeof(V);
+    return at;
+  }
+};
+
+template <typename T>
+struct NaPtrs {
+  Dev<T> d;
+  int *plen, *cur_n, *alen, *cur_m, *tmp_ci, *err, *flag;
+  double* tmp_raw;
+  int4 *kn_chunks, *a_chunks;
+  int *kn_long, *a_long;
+};
+
+// Carve the scratch array; base == nullptr only measures.
+template <typename T>
+__host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p) {
+  NaLayout<T> L;
+  const size_t n = in.n, m = in.m;
+  const size_t nkn = 2 * (size_t)in.nnzP + in.nnzA;  // full P ≤ twice its upper triangle
+  const size_t na = in.nnzA;
+  const size_t tmpn = nkn > na ? nkn : na;
+  const size_t ch_kn = nkn / kChunk + nkn / 257 + 1, lr_kn = nkn / 257 + 1;
+  const size_t ch_a = na / kChunk + na / 257 + 1, lr_a = na / 257 + 1;
+  size_t o[64];
+  int c = 0;
+  o[c++] = L.template take<int>(n + 1);       // 0 kn_rp
+  o[c++] = L.template take<int>(nkn);         // 1 kn_ci
+  o[c++] = L.template take<T>(nkn);           // 2 kn_v
+  o[c++] = L.template take<double>(nkn);      // 3 kn_raw
+  o[c++] = L.template take<int>(m + 1);       // 4 a_rp
+  o[c++] = L.template take<int>(na);          // 5 a_ci
+  o[c++] = L.template take<T>(na);            // 6 a_v
+  o[c++] = L.template take<double>(na);       // 7 a_raw
+  o[c++] = L.template take<int>(tmpn);        // 8 tmp_ci
+  o[c++] = L.template take<double>(tmpn);     // 9 tmp_raw
+  o[c++] = L.template take<int>(n);           // 10 plen
+  o[c++] = L.template take<int>(n);           // 11 cur_n
+  o[c++] = L.template take<int>(m);           // 12 alen
+  o[c++] = L.template take<int>(m);           // 13 cur_m
+  o[c++] = L.template take<int4>(ch_kn);      // 14 kn chunks
+  o[c++] = L.template take<int>(lr_kn);       // 15 kn long rows
+  o[c++] = L.template take<int4>(ch_a);       // 16 a chunks
+  o[c++] = L.template take<int>(lr_a);        // 17 a long rows
+  o[c++] = L.template take<uint8_t>(m);       // 18 rtype
+  const int nvec_n = 14, nvec_m = 18;
+  const int first_n = c;
+  for (int k = 0; k < nvec_n; ++k) o[c++] = L.template take<double>(n);
+  const int first_m = c;
+  for (int k = 0; k < nvec_m; ++k) o[c++] = L.template take<double>(m);
+  const int first_tn = c;
+  for (int k = 0; k < 7; ++k) o[c++] = L.template take<T>(n);
+  const int at_rt = c;
+  o[c++] = L.template take<T>(m);
+  const int at_sc = c;
+  o[c++] = L.template take<Scalars>(1);
+  const int at_err = c;
+  o[c++] = L.template take<int>(2);
+  if (base && p) {
+    Dev<T>& d = p->d;
+    d.n = in.n;
+    d.m = in.m;
+    d.kn_rp = (const int*)(base + o[0]);
+    d.kn_ci = (const int*)(base + o[1]);
+    d.kn_v = (T*)(base + o[2]);
+    d.kn_raw = (const double*)(base + o[3]);
+    d.a_rp = (const int*)(base + o[4]);
+    d.a_ci = (const int*)(base + o[5]);
+    d.a_v = (T*)(base + o[6]);
+    d.a_raw = (const double*)(base + o[7]);
+    p->tmp_ci = (int*)(base + o[8]);
+    p->tmp_raw = (double*)(base + o[9]);
+    p->plen = (int*)(base + o[10]);
+    p->cur_n = (int*)(base + o[11]);
+    p->alen = (int*)(base + o[12]);
+    p->cur_m = (int*)(base + o[13]);
+    p->kn_chunks = (int4*)(base + o[14]);
+    p->kn_long = (int*)(base + o[15]);
+    p->a_chunks = (int4*)(base + o[16]);
+    p->a_long = (int*)(base + o[17]);
+    d.rtype = (uint8_t*)(base + o[18]);
+    double** nv[] = {&d.D, &d.q, &d.pdiag, &d.dg, &d.nrm_n, &d.x, &d.dx, &d.px,
+                     &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt};
+    for (int k = 0; k < nvec_n; ++k) *nv[k] = (double*)(base + o[first_n + k]);
+    double** mv[] = {&d.E, &d.l, &d.u, &d.rho, &d.rho_inv, &d.nrm_m, &d.z, &d.y, &d.dy,
+                     &d.ax, &d.adx, &d.azt, &d.z_out, &d.y_out, &d.pcert, &d.zt, &d.wm, &d.um};
+    for (int k = 0; k < nvec_m; ++k) *mv[k] = (double*)(base + o[first_m + k]);
+    T** tv[] = {&d.dinv, &d.r, &d.b, &d.s, &d.p0, &d.p1, &d.Kp};
+    for (int k = 0; k < 7; ++k) *tv[k] = (T*)(base + o[first_tn + k]);
+    d.rt = (T*)(base + o[at_rt]);
+    d.sc = (Scalars*)(base + o[at_sc]);
+    p->err = (int*)(base + o[at_err]);
+    p->flag = p->err + 1;
+    // the caller's inputs are read in place; x and y are written in place
+    d.q_raw = in.q;
+    d.l_raw = in.l;
+    d.u_raw = in.u;
+    d.x_out = in.x;
+    d.y_out = in.y;
+  }
+  return L.total;
+}
+
+// Exclusive prefix sum of v[0..count) into out[0..count] by one CTA.
+__device__ void block_exclusive_scan(const int* v, int* out, int count, int* sh) {
+  // sh: at least blockDim.x/32 + 1 ints
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int carry = 0;
+  for (int base = 0; base < count; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int x = i < count ? v[i] : 0;
+    int incl = x;
+    for (int off = 1; off < 32; off <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    if (lane == 31) sh[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int w = lane < nw ? sh[lane] : 0;
+      int wi = w;
+      for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, wi, off);
+        if (lane >= off) wi += y;
+      }
+      if (lane < nw) sh[lane] = wi - w;  // exclusive warp offsets
+      if (lane == nw - 1) sh[32] = wi;   // chunk total
+    }
+    __syncthreads();
+    if (i < count) out[i] = carry + sh[wid] + incl - x;
+    carry += sh[32];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[count] = carry;
+  __syncthreads();
+}
+
+// Row schedule built on the device (same rule as the host builder of
+// osqp_setup: long rows > max(256, 8·mean) cut into kChunk chunks, sub-warp
+// width = smallest power of two ≥ the mean short-row length).
+__device__ void build_sched(Sched& S, const int* rp, int nrows, int4* chunks, int* long_rows,
+                            int* sh_int, double* sm) {
+  const int nnz = rp[nrows];
+  const double mean_all = nrows > 0 ? (double)nnz / nrows : 0.0;
+  const int thresh = max(256, (int)(8.0 * ceil(mean_all)));
+  double red[2] = {0.0, 0.0};  // short nnz, short rows
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+    const int len = rp[r + 1] - rp[r];
+    if (len <= thresh) {
+      red[0] += len;
+      red[1] += 1.0;
+    }
+  }
+  block_reduce<2>(red, 0u, sm);
+  const double sn = sm[32 * kMaxRed], sc = sm[32 * kMaxRed + 1];
+  __syncthreads();
+  // long rows and their chunks, in row order, by one thread (few long rows)
+  if (threadIdx.x == 0) {
+    int nl = 0, nc = 0;
+    for (int r = 0; r < nrows; ++r) {
+      const int b = rp[r], e = rp[r + 1];
+      if (e - b <= thresh) continue;
+      long_rows[nl++] = r;
+      for (int k = b; k < e; k += kChunk) chunks[nc++] = make_int4(r, k, min(k + kChunk, e), k == b);
+    }
+    sh_int[0] = nl;
+    sh_int[1] = nc;
+  }
+  __syncthreads();
+  const double ms = sc > 0 ? sn / sc : 1.0;
+  // same width rule as the host schedule builder of osqp_setup
+  int g_mean = 1;
+  while (g_mean < 32 && (double)g_mean < ms) g_mean <<= 1;
+  int g_min = 1;
+  while (g_min < 32 && (double)g_min * 16.0 < ms) g_min <<= 1;
+  int g_occ = 1;
+  const long long nshort = (long long)sc, nwarps = blockDim.x / 32;
+  while (g_occ < 32 && (long long)(g_occ * 2) * nshort <= 32LL * nwarps) g_occ <<= 1;
+  const int G = max(g_min, min(g_mean, g_occ));
+  if (threadIdx.x == 0) {
+    S.nrows = nrows;
+    S.group = G;
+    S.long_thresh = thresh;
+    S.nlong = sh_int[0];
+    S.nchunks = sh_int[1];
+    S.chunks = chunks;
+    S.long_rows = long_rows;
+  }
+  __syncthreads();
+}
+
+// Column of CSC entry k (binary search in colptr).
+__device__ __forceinline__ int col_of(const int* cp, int ncols, int k) {
+  int lo = 0, hi = ncols;  // cp[lo] <= k < cp[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (cp[mid] <= k) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_noalloc(NaInput in, const __grid_constant__ Params P,
+                                                       double rho0, char* scratch) {
+  __shared__ double sm[kSmemDoubles];
+  __shared__ NaPtrs<T> sp;
+  __shared__ int sh_int[40];
+  if (threadIdx.x == 0) na_carve<T>(in, scratch, &sp);
+  __syncthreads();
+  Dev<T>& d = sp.d;
+  const int n = in.n, m = in.m, tid = threadIdx.x, nth = blockDim.x;
+  if (tid == 0) {
+    sp.err[0] = kNaOk;
+    *d.sc = Scalars{};
+  }
+  for (int j = tid; j < n; j += nth) {
+    sp.plen[j] = 0;
+  }
+  for (int i = tid; i < m; i += nth) sp.alen[i] = 0;
+  __syncthreads();
+  // --- validate the CSC input (bounds, order, upper triangle of P)
+  for (int j = tid; j < n; j += nth) {
+    const int b = in.Pp[j], e = in.Pp[j + 1];
+    if (b > e || b < 0 || e > in.nnzP) atomicExch(sp.err, kNaBadCsc);
+    const int ba = in.Ap[j], ea = in.Ap[j + 1];
+    if (ba > ea || ba < 0 || ea > in.nnzA) atomicExch(sp.err, kNaBadCsc);
+  }
+  if (tid == 0 && (in.Pp[0] != 0 || in.Pp[n] != in.nnzP || in.Ap[0] != 0 || in.Ap[n] != in.nnzA))
+    atomicExch(sp.err, kNaBadCsc);
+  __syncthreads();
+  if (*(volatile int*)sp.err != kNaOk) {
+    if (tid == 0) d.sc->dev_error = sp.err[0];
+    return;
+  }
+  for (int k = tid; k < in.nnzP; k += nth) {
+    const int j = col_of(in.Pp, n, k), i = in.Pi[k];
+    if (i < 0 || i > j || (k > in.Pp[j] && in.Pi[k - 1] >= i)) atomicExch(sp.err, kNaBadCsc);
+  }
+  for (int k = tid; k < in.nnzA; k += nth) {
+    const int j = col_of(in.Ap, n, k), i = in.Ai[k];
+    if (i < 0 || i >= m || (k > in.Ap[j] && in.Ai[k - 1] >= i)) atomicExch(sp.err, kNaBadCsc);
+  }
+  __syncthreads();
+  if (*(volatile int*)sp.err != kNaOk) {
+    if (tid == 0) d.sc->dev_error = sp.err[0];
+    return;
+  }
+  // --- Kn = [P̄ Āᵀ] rows: full-P part by counting + atomic scatter + rank sort
+  for (int k = tid; k < in.nnzP; k += nth) {
+    const int j = col_of(in.Pp, n, k), i = in.Pi[k];
+    atomicAdd(&sp.plen[i], 1);
+    if (i != j) atomicAdd(&sp.plen[j], 1);
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += nth) sp.cur_n[j] = sp.plen[j] + (in.Ap[j + 1] - in.Ap[j]);
+  __syncthreads();
+  block_exclusive_scan(sp.cur_n, (int*)d.kn_rp, n, sh_int);
+  for (int j = tid; j < n; j += nth) {
+    sp.cur_n[j] = d.kn_rp[j];
+    if (sp.plen[j] > kNoallocMaxRow) atomicExch(sp.err, kNaLongRow);
+  }
+  __syncthreads();
+  for (int k = tid; k < in.nnzP; k += nth) {
+    const int j = col_of(in.Pp, n, k), i = in.Pi[k];
+    int pos = atomicAdd(&sp.cur_n[i], 1);
+    sp.tmp_ci[pos] = j;
+    sp.tmp_raw[pos] = in.Px[k];
+    if (i != j) {
+      pos = atomicAdd(&sp.cur_n[j], 1);
+      sp.tmp_ci[pos] = i;
+      sp.tmp_raw[pos] = in.Px[k];
+    }
+  }
+  for (int k = tid; k < in.nnzA; k += nth) {
+    const int j = col_of(in.Ap, n, k);
+    const int pos = d.kn_rp[j] + sp.plen[j] + (k - in.Ap[j]);
+    ((int*)d.kn_ci)[pos] = n + in.Ai[k];
+    ((double*)d.kn_raw)[pos] = in.Ax[k];
+  }
+  __syncthreads();
+  if (*(volatile int*)sp.err != kNaOk) {
+    if (tid == 0) d.sc->dev_error = sp.err[0];
+    return;
+  }
+  // rank sort of each row's P part by column (unique columns → unique order)
+  for (int e = tid; e < d.kn_rp[n]; e += nth) {
+    const int r = col_of(d.kn_rp, n, e);
+    const int b = d.kn_rp[r], len = sp.plen[r];
+    if (e - b >= len) continue;
+    const int c = sp.tmp_ci[e];
+    int rank = 0;
+    for (int f = b; f < b + len; ++f) rank += sp.tmp_ci[f] < c;
+    ((int*)d.kn_ci)[b + rank] = c;
+    ((double*)d.kn_raw)[b + rank] = sp.tmp_raw[e];
+  }
+  __syncthreads();
+  // --- Ā rows: counting + atomic scatter + rank sort
+  for (int k = tid; k < in.nnzA; k += nth) atomicAdd(&sp.alen[in.Ai[k]], 1);
+  __syncthreads();
+  block_exclusive_scan(sp.alen, (int*)d.a_rp, m, sh_int);
+  for (int i = tid; i < m; i += nth) {
+    sp.cur_m[i] = d.a_rp[i];
+    if (sp.alen[i] > kNoallocMaxRow) atomicExch(sp.err, kNaLongRow);
+  }
+  __syncthreads();
+  if (*(volatile int*)sp.err != kNaOk) {
+    if (tid == 0) d.sc->dev_error = sp.err[0];
+    return;
+  }
+  for (int k = tid; k < in.nnzA; k += nth) {
+    const int j = col_of(in.Ap, n, k);
+    const int pos = atomicAdd(&sp.cur_m[in.Ai[k]], 1);
+    sp.tmp_ci[pos] = j;
+    sp.tmp_raw[pos] = in.Ax[k];
+  }
+  __syncthreads();
+  for (int e = tid; e < in.nnzA; e += nth) {
+    const int r = col_of(d.a_rp, m, e);
+    const int b = d.a_rp[r], len = d.a_rp[r + 1] - b;
+    const int c = sp.tmp_ci[e];
+    int rank = 0;
+    for (int f = b; f < b + len; ++f) rank += sp.tmp_ci[f] < c;
+    ((int*)d.a_ci)[b + rank] = c;
+    ((double*)d.a_raw)[b + rank] = sp.tmp_raw[e];
+  }
+  __syncthreads();
+  // --- schedules, then the same stages as the one-CTA solver
+  if (tid == 0) sh_int[2] = 0;
+  build_sched(d.kn, d.kn_rp, n, sp.kn_chunks, sp.kn_long, sh_int, sm);
+  build_sched(d.as, d.a_rp, m, sp.a_chunks, sp.a_long, sh_int, sm);
+  BlockTeam tm{sm};
+  if (!scale_stage(tm, d, P, rho0, true)) return;
+  admm_stage(tm, d, P);
+}
+
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
+
+// Per-device address of the scratch array (host code must not use the
+// symbol's name as an address).
+int scratch_address(char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OSQP_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return OSQP_ERR_LIMIT;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return OSQP_ERR_CUDA;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = (char*)g_scratch_ptr[dev];
+  return OSQP_OK;
+}
+
+}  // namespace
+
+extern "C" int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_colptr,
+                                      const int32_t* P_rowind, const double* P_val, int32_t P_nnz,
+                                      const double* q, const int32_t* A_colptr,
+                                      const int32_t* A_rowind, const double* A_val, int32_t A_nnz,
+                                      const double* l, const double* u,
+                                      const osqp_settings* settings, double* x, double* y,
+                                      osqp_info* info, void* stream) {
+  if (!settings || !P_colptr || !q || !A_colptr || !x) return OSQP_ERR_ARG;
+  if (n < 1 || m < 0 || P_nnz < 0 || A_nnz < 0) return OSQP_ERR_DIMS;
+  if ((P_nnz && (!P_rowind || !P_val)) || (A_nnz && (!A_rowind || !A_val))) return OSQP_ERR_ARG;
+  if (m > 0 && (!l || !u || !y)) return OSQP_ERR_ARG;
+  const osqp_settings& s = *settings;
+  if (!(s.rho > 0) || !(s.sigma > 0) || !(s.alpha > 0 && s.alpha < 2) || s.max_iter < 0 ||
+      s.check_interval < 1 || s.scaling_iters < 0 || s.pcg_max_iter < 1 ||
+      !(s.eps_abs >= 0) || !(s.eps_rel >= 0) || !(s.eps_pinf > 0) || !(s.eps_dinf > 0) ||
+      !(s.adaptive_rho_tolerance >= 1) || !(s.pcg_tol_fraction >= 0) || !(s.pcg_tol_floor >= 0) ||
+      (s.precision != OSQP_PRECISION_FP64 && s.precision != OSQP_PRECISION_FP32_MIXED))
+    return OSQP_ERR_SETTINGS;
+  NaInput in{n, m, P_nnz, A_nnz, P_colptr, P_rowind, P_val, q, A_colptr, A_rowind, A_val,
+             l, u, x, y};
+  const size_t need = s.precision == OSQP_PRECISION_FP64 ? na_carve<double>(in, nullptr, nullptr)
+                                                        : na_carve<float>(in, nullptr, nullptr);
+  if (need > kNoallocScratchBytes) return OSQP_ERR_LIMIT;
+  char* base = nullptr;
+  int rc = scratch_address(&base);
+  if (rc) return rc;
+  Params P;
+  std::memset(&P, 0, sizeof(P));
+  P.sigma = s.sigma;
+  P.alpha = s.alpha;
+  P.eps_abs = s.eps_abs;
+  P.eps_rel = s.eps_rel;
+  P.eps_pinf = s.eps_pinf;
+  P.eps_dinf = s.eps_dinf;
+  P.rho_tol = s.adaptive_rho_tolerance;
+  P.eps_equil = s.eps_equil;
+  P.pcg_kappa = s.pcg_tol_fraction;
+  P.pcg_floor = s.pcg_tol_floor;
+  P.pcg_reduce = s.precision == OSQP_PRECISION_FP32_MIXED ? 1e-5 : 0.0;
+  P.time_limit_ns = s.time_limit > 0 ? s.time_limit * 1e9 : 0.0;
+  P.max_iter = s.max_iter;
+  P.check_interval = s.check_interval;
+  P.adaptive_rho = s.adaptive_rho;
+  P.scaling_iters = s.scaling_iters;
+  P.max_rho_updates = s.max_rho_updates;
+  P.pcg_max_iter = s.pcg_max_iter;
+  P.barrier_timeout_ns = 2000000000ull;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (s.precision == OSQP_PRECISION_FP64)
+    k_noalloc<double><<<1, kThreads, 0, st>>>(in, P, s.rho, base);
+  else
+    k_noalloc<float><<<1, kThreads, 0, st>>>(in, P, s.rho, base);
+  if (cudaGetLastError() != cudaSuccess) return OSQP_ERR_CUDA;
+  // Scalars sit at a fixed offset of the layout: read them back.
+  Scalars sc;
+  NaPtrs<double> probe64;
+  NaPtrs<float> probe32;
+  const Scalars* dsc = s.precision == OSQP_PRECISION_FP64
+                           ? (na_carve<double>(in, base, &probe64), probe64.d.sc)
+                           : (na_carve<float>(in, base, &probe32), probe32.d.sc);
+  if (cudaMemcpyAsync(&sc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return OSQP_ERR_CUDA;
+  if (sc.dev_error == kNaBadCsc) return OSQP_ERR_CSC;
+  if (sc.dev_error == kNaLongRow) return OSQP_ERR_LIMIT;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = sc.status;
+    info->iter = sc.iter;
+    info->pcg_iters = sc.pcg_iters;
+    info->rho_updates = sc.rho_updates;
+    info->ruiz_passes = sc.ruiz_passes;
+    info->launch = 1;
+    info->obj_val = sc.obj;
+    info->prim_res = sc.prim_res;
+    info->dual_res = sc.dual_res;
+    info->rho_estimate = sc.rho_bar;
+  }
+  return OSQP_OK;
+}

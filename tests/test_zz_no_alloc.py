@@ -1,0 +1,100 @@
+"""osqp_solve_noalloc — the entry point for callers that cannot allocate.
+
+Code inside a CUDA-graph capture, plugins whose host framework owns all
+device memory, and real-time loops that forbid cudaMalloc/cudaFree after
+start-up cannot use osqp_setup, which allocates the solver's device memory.
+osqp_solve_noalloc solves one small QP with every work array inside a fixed,
+statically allocated device buffer.  These tests call it through the C ABI
+and check it against the allocating entry points on two calls in a row.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_1711_08013_gb300 import _binding as B
+from paper_1711_08013_gb300 import problems as pb
+
+_P = C.c_void_p
+
+
+def noalloc_fn():
+    f = B.lib().osqp_solve_noalloc
+    f.restype = C.c_int32
+    f.argtypes = [C.c_int32, C.c_int32, _P, _P, _P, C.c_int32, _P, _P, _P, _P, C.c_int32, _P, _P,
+                  C.POINTER(B.osqp_settings), _P, _P, C.POINTER(B.osqp_info), _P]
+    return f
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    """The size check runs on the host before any device work: a problem
+    needing more than the 16 MiB work array is refused with OSQP_ERR_LIMIT."""
+    st = B.osqp_set_default_settings()
+    info = B.osqp_info()
+    fake = 256  # never dereferenced: the call returns before touching memory
+    rc = noalloc_fn()(2_000_000, 2_000_000, fake, fake, fake, 4_000_000, fake, fake, fake, fake,
+                      8_000_000, fake, fake, C.byref(st), fake, fake, C.byref(info), None)
+    assert rc == B.OSQP_ERR_LIMIT
+
+
+def _device_inputs(torch, qp):
+    dev = torch.device("cuda", 0)
+    t = lambda a, dt: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    return dict(Pp=t(qp.P.indptr, torch.int32), Pi=t(qp.P.indices, torch.int32),
+                Px=t(qp.P.data, torch.float64), q=t(qp.q, torch.float64),
+                Ap=t(qp.A.indptr, torch.int32), Ai=t(qp.A.indices, torch.int32),
+                Ax=t(qp.A.data, torch.float64), l=t(qp.l, torch.float64),
+                u=t(qp.u, torch.float64))
+
+
+def _call(torch, f, qp, d, st, x, y):
+    info = B.osqp_info()
+    x.fill_(float("nan"))
+    y.fill_(float("nan"))
+    rc = f(qp.n, qp.m, d["Pp"].data_ptr(), d["Pi"].data_ptr(), d["Px"].data_ptr(), qp.P.nnz,
+           d["q"].data_ptr(), d["Ap"].data_ptr(), d["Ai"].data_ptr(), d["Ax"].data_ptr(),
+           qp.A.nnz, d["l"].data_ptr(), d["u"].data_ptr(), C.byref(st), x.data_ptr(),
+           y.data_ptr(), C.byref(info), None)
+    torch.cuda.synchronize()
+    return rc, info, x.cpu().numpy().copy(), y.cpu().numpy().copy()
+
+
+# The same exact-solve settings as the iterate-parity tests: fixed ρ, a fixed
+# number of iterations and PCG run to 1e-14·‖rhs‖∞.
+STEP = dict(adaptive_rho=0, eps_abs=0.0, eps_rel=0.0, eps_pinf=1e-300, eps_dinf=1e-300,
+            pcg_tol_fraction=0.0, pcg_tol_floor=1e-14, pcg_max_iter=2000, check_interval=1,
+            max_iter=40)
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,make,kw", [
+    ("random_qp_exact", lambda: pb.random_qp(40, 160, seed=21), STEP),
+    ("portfolio_exact", lambda: pb.portfolio(3, seed=22), STEP),          # long rows
+    ("mpc_default", lambda: pb.mpc(6, 8, seed=23), {}),
+    ("lasso_fp32_default", lambda: pb.lasso(4, seed=24), dict(precision=B.FP32_MIXED)),
+])
+def test_noalloc_matches_allocating_entry_point_twice(name, make, kw):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_08013_gb300.solver import Solver
+    torch.cuda.set_device(0)
+    qp = make()
+    with Solver(qp, launch=1, **kw) as s:
+        ref = s.solve()
+    d = _device_inputs(torch, qp)
+    x = torch.empty(qp.n, dtype=torch.float64, device="cuda")
+    y = torch.empty(qp.m, dtype=torch.float64, device="cuda")
+    st = B.osqp_set_default_settings(launch=1, **kw)
+    f = noalloc_fn()
+    for call in range(2):
+        rc, info, xg, yg = _call(torch, f, qp, d, st, x, y)
+        assert rc == B.OSQP_OK, (name, call, rc)
+        assert info.status == ref.status and info.iter == ref.iter, (name, call)
+        assert _rel(xg, ref.x) <= 1e-8, (name, call, _rel(xg, ref.x))
+        assert _rel(yg, ref.y) <= 1e-8, (name, call, _rel(yg, ref.y))
+        assert abs(info.obj_val - ref.obj_val) <= 1e-8 * max(1.0, abs(ref.obj_val))
