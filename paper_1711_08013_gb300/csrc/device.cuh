@@ -25,7 +25,8 @@ namespace osqpgb {
 
 constexpr int kThreads = 512;   // threads per CTA of every team kernel
 constexpr int kMaxRed = 32;     // reduction slots
-constexpr int kSmemDoubles = 34 * kMaxRed;
+constexpr int kMaxSumSlots = 4; // sum slots staged through shared memory per reduction
+constexpr int kSmemDoubles = 34 * kMaxRed + kMaxSumSlots * kThreads;
 constexpr int kChunk = 256;     // nonzeros per long-row chunk
 
 constexpr uint8_t kLInf = 1, kUInf = 2, kEq = 4;  // row-type bits
@@ -79,11 +80,14 @@ struct Dev {
   Sched as;
   const double *q_raw, *l_raw, *u_raw;
   uint8_t* rtype;
-  double *D, *E, *q, *l, *u, *rho, *rho_inv, *pdiag, *dg, *nrm_n, *nrm_m;
+  double *D, *E, *Dinv, *Einv, *q, *l, *u, *rho, *rho_inv, *pdiag, *dg, *nrm_n, *nrm_m;
   T* dinv;
   double *x, *z, *y, *dx, *dy;
   double *xt, *zt, *wm, *um;  // x̃, z̃ and the RHS inputs stay FP64 in both modes
-  T *r, *b, *s, *p0, *p1, *Kp, *rt;
+  // PCG vectors (working precision): b, mr = M⁻¹r, p; r, s = Kp, w = K·mr
+  // and t = R·Ā·mr double-buffered; ap = Āp (for z̃ = Āx̃)
+  T *b, *mr, *p, *r0, *r1, *s0, *s1, *w0, *w1;
+  T *rt0, *rt1, *ap;
   double *px, *aty, *pdx, *atdy, *ax, *adx, *azt;
   double *x_out, *y_out, *z_out, *pcert, *dcert;
   Scalars* sc;
@@ -111,35 +115,81 @@ __device__ __forceinline__ double red_identity(unsigned maxmask, int k) {
   return ((maxmask >> k) & 1u) ? -INFINITY : 0.0;
 }
 
-// Block-wide reduction of K slots; slot k is a max when bit k of maxmask is
-// set, else a sum.  Result left in sm[32*kMaxRed + k].  All threads call it.
-template <int K>
-__device__ __forceinline__ void block_reduce(const double (&v)[K], unsigned maxmask, double* sm) {
+// Order-preserving 64-bit key of a double: max reductions run on integers,
+// off the narrow FP64 pipe.  NaN keys above +∞, so a NaN propagates.
+__device__ __forceinline__ unsigned long long dkey(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dunkey(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+
+// Block-wide reduction of K slots; slot k is a max when bit k of MAXMASK is
+// set, else a sum.  Max slots: integer keys combined by warp shuffles.  Sum
+// slots (at most kMaxSumSlots): every thread stages its value in shared
+// memory and one warp per slot adds the column (16 values per lane, then a
+// 5-level shuffle tree), about a quarter of the FP64 instructions of a
+// per-warp shuffle tree.  Result left in sm[32*kMaxRed + k].  All threads
+// call it.
+template <int K, unsigned MAXMASK>
+__device__ __forceinline__ void block_reduce(const double (&v)[K], double* sm) {
+  static_assert(K <= kMaxRed, "too many reduction slots");
+  constexpr int S = K - __builtin_popcount(MAXMASK & ((1u << K) - 1u));
+  static_assert(S <= kMaxSumSlots, "too many sum slots");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long* smk = reinterpret_cast<unsigned long long*>(sm);
+  double* stage = sm + 34 * kMaxRed;
+  int sidx = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const bool mx = (maxmask >> k) & 1u;
-    double x = v[k];
+    if ((MAXMASK >> k) & 1u) {
+      unsigned long long x = dkey(v[k]);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      double y = __shfl_xor_sync(0xffffffffu, x, off);
-      x = mx ? fmax(x, y) : x + y;
+      for (int off = 16; off > 0; off >>= 1) x = umax64(x, __shfl_xor_sync(0xffffffffu, x, off));
+      if (lane == 0) smk[wid * kMaxRed + k] = x;
+    } else {
+      stage[sidx * blockDim.x + threadIdx.x] = v[k];
+      ++sidx;
     }
-    if (lane == 0) sm[wid * kMaxRed + k] = x;
   }
   __syncthreads();
   if (wid == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const bool mx = (maxmask >> k) & 1u;
-      double x = lane < nw ? sm[lane * kMaxRed + k] : red_identity(maxmask, k);
+      if ((MAXMASK >> k) & 1u) {
+        unsigned long long x = lane < nw ? smk[lane * kMaxRed + k] : 0ull;
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        double y = __shfl_xor_sync(0xffffffffu, x, off);
-        x = mx ? fmax(x, y) : x + y;
+        for (int off = 16; off > 0; off >>= 1) x = umax64(x, __shfl_xor_sync(0xffffffffu, x, off));
+        if (lane == 0) sm[32 * kMaxRed + k] = dunkey(x);
       }
-      if (lane == 0) sm[32 * kMaxRed + k] = x;
     }
+  }
+  // sum slot j is reduced by warp j (slot k is the j-th sum slot)
+  if (S > 0 && wid < S) {
+    int kk = -1, j = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (!((MAXMASK >> k) & 1u)) {
+        if (j == wid) kk = k;
+        ++j;
+      }
+    const double* col = stage + wid * blockDim.x;
+    double t[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) t[u] = lane + 32 * u < (int)blockDim.x ? col[lane + 32 * u] : 0.0;
+#pragma unroll
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+      for (int u = 0; u < w; ++u) t[u] += t[u + w];
+    double x = t[0];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) sm[32 * kMaxRed + kk] = x;
   }
   __syncthreads();
 }
@@ -194,9 +244,9 @@ struct GridTeam {
     return sm[34 * kMaxRed - 1] != 0.0;
   }
 
-  template <int K>
-  __device__ void publish(const double (&v)[K], unsigned maxmask) {
-    block_reduce<K>(v, maxmask, sm);
+  template <int K, unsigned MAXMASK>
+  __device__ void publish(const double (&v)[K]) {
+    block_reduce<K, MAXMASK>(v, sm);
     if (threadIdx.x < K)
       part[((size_t)buf * gridDim.x + blockIdx.x) * kMaxRed + threadIdx.x] =
           sm[32 * kMaxRed + threadIdx.x];
@@ -204,22 +254,37 @@ struct GridTeam {
 
   // Combine the partials of the last publish (after a sync).  Every CTA runs
   // the same fixed-order combination, so all threads see identical values.
-  template <int K>
-  __device__ void collect(double (&out)[K], unsigned maxmask) {
+  // Each lane issues all of its (≤ 16) partial loads before combining them.
+  template <int K, unsigned MAXMASK>
+  __device__ void collect(double (&out)[K]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nb = gridDim.x;
     for (int k = wid; k < K; k += nw) {
-      const bool mx = (maxmask >> k) & 1u;
-      double x = red_identity(maxmask, k);
-      for (int b = lane; b < (int)gridDim.x; b += 32) {
-        double y = __ldcg(&part[((size_t)buf * gridDim.x + b) * kMaxRed + k]);
-        x = mx ? fmax(x, y) : x + y;
-      }
+      const bool mx = (MAXMASK >> k) & 1u;
+      const double* src = part + (size_t)buf * nb * kMaxRed + k;
+      double y[16];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        double y = __shfl_xor_sync(0xffffffffu, x, off);
-        x = mx ? fmax(x, y) : x + y;
+      for (int u = 0; u < 16; ++u) {
+        const int b = lane + 32 * u;
+        y[u] = b < nb ? __ldcg(src + (size_t)b * kMaxRed) : (mx ? -INFINITY : 0.0);
       }
-      if (lane == 0) sm[33 * kMaxRed + k] = x;
+      if (mx) {
+        unsigned long long x = dkey(y[0]);
+#pragma unroll
+        for (int u = 1; u < 16; ++u) x = umax64(x, dkey(y[u]));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x = umax64(x, __shfl_xor_sync(0xffffffffu, x, off));
+        if (lane == 0) sm[33 * kMaxRed + k] = dunkey(x);
+      } else {
+#pragma unroll
+        for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+          for (int u = 0; u < w; ++u) y[u] += y[u + w];
+        double x = y[0];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0) sm[33 * kMaxRed + k] = x;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -239,12 +304,12 @@ struct BlockTeam {
     __syncthreads();
     return true;
   }
-  template <int K>
-  __device__ void publish(const double (&v)[K], unsigned maxmask) {
-    block_reduce<K>(v, maxmask, sm);
+  template <int K, unsigned MAXMASK>
+  __device__ void publish(const double (&v)[K]) {
+    block_reduce<K, MAXMASK>(v, sm);
   }
-  template <int K>
-  __device__ void collect(double (&out)[K], unsigned) {
+  template <int K, unsigned MAXMASK>
+  __device__ void collect(double (&out)[K]) {
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = sm[32 * kMaxRed + k];
   }
@@ -455,9 +520,9 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
       d.E[i] *= dl;
       dev[0] = fmax(dev[0], fabs(1.0 - dl));
     }
-    tm.template publish<1>(dev, 1u);
+    tm.template publish<1, 1u>(dev);
     if (!tm.sync()) return false;
-    tm.template collect<1>(dev, 1u);
+    tm.template collect<1, 1u>(dev);
     ++passes;
     // Cost scaling γ = 1/max{mean_j ‖P̄_:,j‖∞, ‖q̄‖∞} with the new D.
     spmv<1, true, double, double>(
@@ -469,17 +534,17 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
         [&](int j, int, double* acc) { atomic_max_nonneg(&d.nrm_n[j], cc * d.D[j] * acc[0]); });
     double qn[1] = {0.0};
     for (int j = tid; j < n; j += nth) qn[0] = fmax(qn[0], fabs(cc * d.D[j] * d.q_raw[j]));
-    tm.template publish<1>(qn, 1u);
+    tm.template publish<1, 1u>(qn);
     if (!tm.sync()) return false;
-    tm.template collect<1>(qn, 1u);
+    tm.template collect<1, 1u>(qn);
     double sum[1] = {0.0};
     for (int j = tid; j < n; j += nth) {
       sum[0] += d.nrm_n[j];
       d.nrm_n[j] = 0.0;
     }
-    tm.template publish<1>(sum, 0u);
+    tm.template publish<1, 0u>(sum);
     if (!tm.sync()) return false;
-    tm.template collect<1>(sum, 0u);
+    tm.template collect<1, 0u>(sum);
     const double mx = fmax(sum[0] / (double)n, qn[0]);
     const double gamma = mx < kNormMin ? 1.0 : 1.0 / mx;
     c *= gamma;
@@ -500,8 +565,12 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
   });
   foreach_entry<double>(tm, d.as, d.a_rp,
                         [&](int i, int k) { d.a_v[k] = T(d.E[i] * d.a_raw[k] * d.D[d.a_ci[k]]); });
-  for (int j = tid; j < n; j += nth) d.q[j] = c * d.D[j] * d.q_raw[j];
+  for (int j = tid; j < n; j += nth) {
+    d.q[j] = c * d.D[j] * d.q_raw[j];
+    d.Dinv[j] = 1.0 / d.D[j];
+  }
   for (int i = tid; i < m; i += nth) {
+    d.Einv[i] = 1.0 / d.E[i];
     const uint8_t t = d.rtype[i];
     d.l[i] = (t & kLInf) ? -INFINITY : d.E[i] * d.l_raw[i];
     d.u[i] = (t & kUInf) ? INFINITY : d.E[i] * d.u_raw[i];
@@ -589,11 +658,15 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   double* __restrict__ zt = d.zt;
   double* __restrict__ wm = d.wm;
   double* __restrict__ um = d.um;
-  T* __restrict__ r = d.r;
   T* __restrict__ bv = d.b;
-  T* __restrict__ s = d.s;
-  T* __restrict__ Kp = d.Kp;
-  T* __restrict__ rt = d.rt;
+  T* __restrict__ u = d.mr;  // u = M⁻¹r
+  T* __restrict__ pv = d.p;
+  T* __restrict__ ap = d.ap;
+  // double-buffer selection without a local-memory pointer table
+  auto rbuf = [&](int i) { return i ? d.r1 : d.r0; };
+  auto sbuf = [&](int i) { return i ? d.s1 : d.s0; };
+  auto wbuf = [&](int i) { return i ? d.w1 : d.w0; };
+  auto tbuf = [&](int i) { return i ? d.rt1 : d.rt0; };
   T* __restrict__ dinv = d.dinv;
   const double* __restrict__ rho = d.rho;
   const double* __restrict__ rho_inv = d.rho_inv;
@@ -601,6 +674,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   int status = kUnsolved, k = 0, pcg_total = 0, rho_updates = 0, checks = 0;
   bool dinv_dirty = false, have_check = false;
   double rp_bar = 0.0, rd_bar = 0.0, prim_res = NAN, dual_res = NAN, obj = NAN;
+  int cur = 0;
 
   // Right-hand-side inputs of the first iteration from the current iterates.
   for (int i = tid; i < m; i += nth) {
@@ -608,8 +682,9 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     wm[i] = rh * z[i] - y[i];
     um[i] = rh * (z[i] - zt[i]) - y[i];
   }
-  zero_long(tm, d.kn, r);
+  zero_long(tm, d.kn, rbuf(cur));
   zero_long(tm, d.kn, bv);
+  zero_long(tm, d.as, tbuf(cur));
   if (!tm.sync()) return false;
 
   for (k = 1; k <= P.max_iter; ++k) {
@@ -622,120 +697,175 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       for (int j = tid; j < n; j += nth) dinv[j] = T(1.0 / d.dg[j]);
       dinv_dirty = false;
     }
-    spmv<2, false, double, T>(
-        tm, d.kn, kn_rp, kn_ci, kn_v,
-        [&](int col, T v, double* acc) {
-          const double vv = (double)v;
-          if (col < n) {
-            acc[0] -= vv * xt[col];
-          } else {
-            acc[0] += vv * um[col - n];
-            acc[1] += vv * wm[col - n];
-          }
-        },
-        [&](int j, double* acc) {
-          const double bj = sigma * x[j] - d.q[j];
-          r[j] = T(bj - sigma * xt[j] + acc[0]);
-          bv[j] = T(bj + acc[1]);
-        },
-        [&](int j, int first, double* acc) {
-          const double bj = first ? sigma * x[j] - d.q[j] : 0.0;
-          const double xs = first ? sigma * xt[j] : 0.0;
-          atomicAdd(&r[j], T(bj - xs + acc[0]));
-          atomicAdd(&bv[j], T(bj + acc[1]));
-        });
+    {
+      T* __restrict__ r = rbuf(cur);
+      spmv<2, false, double, T>(
+          tm, d.kn, kn_rp, kn_ci, kn_v,
+          [&](int col, T v, double* acc) {
+            const double vv = (double)v;
+            if (col < n) {
+              acc[0] -= vv * xt[col];
+            } else {
+              acc[0] += vv * um[col - n];
+              acc[1] += vv * wm[col - n];
+            }
+          },
+          [&](int j, double* acc) {
+            const double bj = sigma * x[j] - d.q[j];
+            r[j] = T(bj - sigma * xt[j] + acc[0]);
+            bv[j] = T(bj + acc[1]);
+          },
+          [&](int j, int first, double* acc) {
+            const double bj = first ? sigma * x[j] - d.q[j] : 0.0;
+            const double xs = first ? sigma * xt[j] : 0.0;
+            atomicAdd(&r[j], T(bj - xs + acc[0]));
+            atomicAdd(&bv[j], T(bj + acc[1]));
+          });
+    }
     if (!tm.sync()) return false;
 
-    // --- A0: s = p = M⁻¹r; t = Ā p computed on the fly; rs, ‖r‖∞, ‖b‖∞
-    T* pc = d.p0;
-    T* pn = d.p1;
+    // PCG on K = P̄ + σI + ĀᵀRĀ in the single-reduction form of Chronopoulos
+    // and Gear: per iteration one stage that updates p, s = Kp, x̃, r, u = M⁻¹r
+    // and computes t = RĀu with u formed on the fly, and one stage that forms
+    // w = Ku and the two inner products (r,u), (w,u).  r, s, w and t are
+    // double-buffered so that gathers never see a vector being rewritten.
+    // --- A0: u = M⁻¹r, t = RĀu; (r,u), ‖r‖∞, ‖b‖∞
     double red3[3] = {0.0, 0.0, 0.0};
-    for (int j = tid; j < n; j += nth) {
-      const T rj = r[j];
-      const T sj = rj * dinv[j];
-      s[j] = sj;
-      pc[j] = sj;
-      red3[0] += (double)rj * (double)sj;
-      red3[1] = fmax(red3[1], fabs((double)rj));
-      red3[2] = fmax(red3[2], fabs((double)bv[j]));
+    {
+      const T* __restrict__ r = rbuf(cur);
+      T* __restrict__ t = tbuf(cur);
+      for (int j = tid; j < n; j += nth) {
+        const T rj = r[j];
+        const T uj = rj * dinv[j];
+        u[j] = uj;
+        red3[0] += (double)rj * (double)uj;
+        red3[1] = fmax(red3[1], fabs((double)rj));
+        red3[2] = fmax(red3[2], fabs((double)bv[j]));
+      }
+      spmv<1, false, T, T>(
+          tm, d.as, a_rp, a_ci, a_v,
+          [&](int col, T v, T* acc) { acc[0] += v * (r[col] * dinv[col]); },
+          [&](int i, T* acc) { t[i] = T(rho[i] * (double)acc[0]); },
+          [&](int i, int, T* acc) { atomicAdd(&t[i], T(rho[i] * (double)acc[0])); });
+      zero_long(tm, d.kn, wbuf(cur));
     }
-    spmv<1, false, T, T>(
-        tm, d.as, a_rp, a_ci, a_v, [&](int col, T v, T* acc) { acc[0] += v * (r[col] * dinv[col]); },
-        [&](int i, T* acc) { rt[i] = T(rho[i] * (double)acc[0]); },
-        [&](int i, int, T* acc) { atomicAdd(&rt[i], T(rho[i] * (double)acc[0])); });
-    zero_long(tm, d.kn, Kp);
-    tm.template publish<3>(red3, 6u);
+    tm.template publish<3, 6u>(red3);
     if (!tm.sync()) return false;
-    tm.template collect<3>(red3, 6u);
-    double rs = red3[0];
+    tm.template collect<3, 6u>(red3);
+    double gamma = red3[0];
     const double bnorm = red3[2];
     // PCG accuracy (reading of "up to some predefined accuracy", §3.1).
     const double tol = fmax(fmax(P.pcg_floor * bnorm, P.pcg_reduce * red3[1]),
                             have_check ? P.pcg_kappa * fmin(rp_bar, rd_bar) : 0.1 * P.pcg_kappa * bnorm);
     bool done = !(red3[1] > tol);
-    int j_it = 0;
-    while (!done) {
-      // --- B: Kp = P̄p + σp + Āᵀ(Rt) and pᵀKp
+    double alpha_c = 0.0, beta_c = 0.0;
+    if (!done) {
+      // --- W: w = Ku, (w,u)
       double red1[1] = {0.0};
+      T* __restrict__ w = wbuf(cur);
+      const T* __restrict__ tg = tbuf(cur);
       spmv<1, false, T, T>(
           tm, d.kn, kn_rp, kn_ci, kn_v,
-          [&](int col, T v, T* acc) { acc[0] += v * (col < n ? pc[col] : rt[col - n]); },
+          [&](int col, T v, T* acc) { acc[0] += v * (col < n ? u[col] : tg[col - n]); },
           [&](int j, T* acc) {
-            const T kp = T(sigma) * pc[j] + acc[0];
-            Kp[j] = kp;
-            red1[0] += (double)pc[j] * (double)kp;
+            const T wj = T(sigma) * u[j] + acc[0];
+            w[j] = wj;
+            red1[0] += (double)wj * (double)u[j];
           },
           [&](int j, int first, T* acc) {
-            const T part = acc[0] + (first ? T(sigma) * pc[j] : T(0));
-            atomicAdd(&Kp[j], part);
-            red1[0] += (double)pc[j] * (double)part;
+            const T part = acc[0] + (first ? T(sigma) * u[j] : T(0));
+            atomicAdd(&w[j], part);
+            red1[0] += (double)part * (double)u[j];
           });
-      tm.template publish<1>(red1, 0u);
+      tm.template publish<1, 0u>(red1);
       if (!tm.sync()) return false;
-      tm.template collect<1>(red1, 0u);
-      if (!(red1[0] > 0.0)) break;  // pᵀKp ≤ 0 only when p vanished (K ≻ 0)
-      const double a = rs / red1[0];
-      const T aT = T(a);
-      // --- C: x̃ += αp, r −= αKp, s = M⁻¹r, z̃ += αt
-      double red2[2] = {0.0, 0.0};
-      for (int j = tid; j < n; j += nth) {
-        xt[j] += a * (double)pc[j];
-        const T rj = r[j] - aT * Kp[j];
-        r[j] = rj;
-        const T sj = rj * dinv[j];
-        s[j] = sj;
-        red2[0] += (double)rj * (double)sj;
-        red2[1] = fmax(red2[1], fabs((double)rj));
+      tm.template collect<1, 0u>(red1);
+      if (red1[0] > 0.0) alpha_c = gamma / red1[0];
+      else done = true;
+    }
+    int j_it = 0;
+    while (!done) {
+      const int nxt = cur ^ 1;
+      const bool first = j_it == 0;
+      const T aT = T(alpha_c), bT = T(beta_c);
+      // --- P1: p = u + βp, s = w + βs, x̃ += αp, r −= αs, u = M⁻¹r,
+      //         Āp = t/ρ + β·Āp, z̃ += α·Āp   (elementwise)
+      {
+        const T* __restrict__ rc = rbuf(cur);
+        const T* __restrict__ sc = sbuf(cur);
+        const T* __restrict__ wc = wbuf(cur);
+        T* __restrict__ rn = rbuf(nxt);
+        T* __restrict__ sn = sbuf(nxt);
+        const T* __restrict__ tc = tbuf(cur);
+        for (int j = tid; j < n; j += nth) {
+          const T pj = first ? u[j] : u[j] + bT * pv[j];
+          const T sj = first ? wc[j] : wc[j] + bT * sc[j];
+          pv[j] = pj;
+          sn[j] = sj;
+          xt[j] += alpha_c * (double)pj;
+          const T rj = rc[j] - aT * sj;
+          rn[j] = rj;
+          u[j] = rj * dinv[j];
+        }
+        for (int i = tid; i < m; i += nth) {
+          const T ti = T(rho_inv[i] * (double)tc[i]);
+          const T api = first ? ti : ti + bT * ap[i];
+          ap[i] = api;
+          zt[i] += alpha_c * (double)api;
+        }
+        zero_long(tm, d.kn, wbuf(nxt));
       }
-      for (int i = tid; i < m; i += nth) {
-        zt[i] += a * rho_inv[i] * (double)rt[i];
-        if (a_rp[i + 1] - a_rp[i] > d.as.long_thresh) rt[i] = T(0);
-      }
-      tm.template publish<2>(red2, 2u);
       if (!tm.sync()) return false;
-      tm.template collect<2>(red2, 2u);
+      // --- P1b: t' = RĀu
+      {
+        T* __restrict__ tn = tbuf(nxt);
+        spmv<1, false, T, T>(
+            tm, d.as, a_rp, a_ci, a_v, [&](int col, T v, T* acc) { acc[0] += v * u[col]; },
+            [&](int i, T* acc) { tn[i] = T(rho[i] * (double)acc[0]); },
+            [&](int i, int, T* acc) { atomicAdd(&tn[i], T(rho[i] * (double)acc[0])); });
+      }
+      if (!tm.sync()) return false;
       ++j_it;
       ++pcg_total;
-      if (!(red2[1] > tol) || j_it >= P.pcg_max_iter) break;
-      const double beta = red2[0] / rs;
-      rs = red2[0];
-      const T bT = T(beta);
-      // --- A: p ← s + βp (new buffer), t = Āp on the fly
-      for (int j = tid; j < n; j += nth) pn[j] = s[j] + bT * pc[j];
-      spmv<1, false, T, T>(
-          tm, d.as, a_rp, a_ci, a_v,
-          [&](int col, T v, T* acc) { acc[0] += v * (s[col] + bT * pc[col]); },
-          [&](int i, T* acc) { rt[i] = T(rho[i] * (double)acc[0]); },
-          [&](int i, int, T* acc) { atomicAdd(&rt[i], T(rho[i] * (double)acc[0])); });
-      zero_long(tm, d.kn, Kp);
+      // --- P2: w = Ku, (r,u), (w,u), ‖r‖∞
+      double red2[3] = {0.0, 0.0, 0.0};
+      {
+        const T* __restrict__ rn = rbuf(nxt);
+        T* __restrict__ wn = wbuf(nxt);
+        for (int j = tid; j < n; j += nth) {
+          const T rj = rn[j];
+          red2[0] += (double)rj * (double)u[j];
+          red2[2] = fmax(red2[2], fabs((double)rj));
+        }
+        const T* __restrict__ tg = tbuf(nxt);
+        spmv<1, false, T, T>(
+            tm, d.kn, kn_rp, kn_ci, kn_v,
+            [&](int col, T v, T* acc) { acc[0] += v * (col < n ? u[col] : tg[col - n]); },
+            [&](int j, T* acc) {
+              const T wj = T(sigma) * u[j] + acc[0];
+              wn[j] = wj;
+              red2[1] += (double)wj * (double)u[j];
+            },
+            [&](int j, int first2, T* acc) {
+              const T part = acc[0] + (first2 ? T(sigma) * u[j] : T(0));
+              atomicAdd(&wn[j], part);
+              red2[1] += (double)part * (double)u[j];
+            });
+        zero_long(tm, d.as, tbuf(cur));
+      }
+      tm.template publish<3, 4u>(red2);
       if (!tm.sync()) return false;
-      T* tmp = pc;
-      pc = pn;
-      pn = tmp;
+      tm.template collect<3, 4u>(red2);
+      cur = nxt;
+      if (!(red2[2] > tol) || j_it >= P.pcg_max_iter) break;
+      const double gamma_n = red2[0];
+      const double beta_n = gamma_n / gamma;
+      const double denom = red2[1] - beta_n * gamma_n / alpha_c;
+      if (!(denom > 0.0) || !(gamma_n > 0.0)) break;  // breakdown: p vanished
+      beta_c = beta_n;
+      alpha_c = gamma_n / denom;
+      gamma = gamma_n;
     }
-    // A long-row entry of rt may still hold this iteration's value when PCG
-    // stopped after stage B: clear it for the next A0.
-    for (int i = tid; i < d.as.nlong; i += nth) rt[d.as.long_rows[i]] = T(0);
 
     // --- U: Algorithm 1 steps 5–7, y in the form ρ(v − Π(v)) of Eq. (zy-update)
     for (int j = tid; j < n; j += nth) {
@@ -755,8 +885,9 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       wm[i] = rh * zn - yn;
       um[i] = rh * (zn - zti) - yn;
     }
-    zero_long(tm, d.kn, r);
+    zero_long(tm, d.kn, rbuf(cur));
     zero_long(tm, d.kn, bv);
+    zero_long(tm, d.as, tbuf(cur));
     const bool check = (k % P.check_interval == 0) || (k == P.max_iter);
     if (check) {
       zero_long(tm, d.kn, d.px);
@@ -832,10 +963,10 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     R[20] = -INFINITY;
     constexpr unsigned kMaxMask = 0xFFFFFFu & ~((1u << 15) | (1u << 18) | (1u << 21) | (1u << 22));
     for (int i = tid; i < m; i += nth) {
-      const double Ei = d.E[i], axi = d.ax[i], zi = z[i];
-      R[0] = fmax(R[0], fabs((axi - zi) / Ei));
-      R[1] = fmax(R[1], fabs(axi / Ei));
-      R[2] = fmax(R[2], fabs(zi / Ei));
+      const double Ei = d.E[i], Eii = d.Einv[i], axi = d.ax[i], zi = z[i];
+      R[0] = fmax(R[0], fabs((axi - zi) * Eii));
+      R[1] = fmax(R[1], fabs(axi * Eii));
+      R[2] = fmax(R[2], fabs(zi * Eii));
       R[3] = fmax(R[3], fabs(axi - zi));
       R[4] = fmax(R[4], fabs(axi));
       R[5] = fmax(R[5], fabs(zi));
@@ -845,7 +976,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       R[14] = fmax(R[14], fabs(Ei * dv));
       if (dv > 0.0) R[15] += d.u[i] * dv;
       else if (dv < 0.0) R[15] += d.l[i] * dv;
-      const double a = d.adx[i] / Ei;
+      const double a = d.adx[i] * Eii;
       const bool lf = !(t & kLInf), uf = !(t & kUInf);
       const double viol = (lf && uf) ? fabs(a) : (lf ? -a : (uf ? a : -INFINITY));
       R[20] = fmax(R[20], viol);
@@ -855,29 +986,29 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       um[i] = rho[i] * (zi - azi) - y[i];
     }
     for (int j = tid; j < n; j += nth) {
-      const double Dj = d.D[j], pxj = d.px[j], atyj = d.aty[j], qj = d.q[j];
+      const double Dj = d.D[j], Dij = d.Dinv[j], pxj = d.px[j], atyj = d.aty[j], qj = d.q[j];
       const double rd = pxj + qj + atyj;
-      R[6] = fmax(R[6], fabs(rd / Dj));
-      R[7] = fmax(R[7], fabs(pxj / Dj));
-      R[8] = fmax(R[8], fabs(atyj / Dj));
-      R[9] = fmax(R[9], fabs(qj / Dj));
+      R[6] = fmax(R[6], fabs(rd * Dij));
+      R[7] = fmax(R[7], fabs(pxj * Dij));
+      R[8] = fmax(R[8], fabs(atyj * Dij));
+      R[9] = fmax(R[9], fabs(qj * Dij));
       R[10] = fmax(R[10], fabs(rd));
       R[11] = fmax(R[11], fabs(pxj));
       R[12] = fmax(R[12], fabs(atyj));
       R[13] = fmax(R[13], fabs(qj));
-      R[16] = fmax(R[16], fabs(d.atdy[j] / Dj));
+      R[16] = fmax(R[16], fabs(d.atdy[j] * Dij));
       const double dxj = d.dx[j];
       R[17] = fmax(R[17], fabs(Dj * dxj));
       R[18] += qj * dxj;
-      R[19] = fmax(R[19], fabs(d.pdx[j] / Dj));
+      R[19] = fmax(R[19], fabs(d.pdx[j] * Dij));
       R[21] += x[j] * pxj;
       R[22] += qj * x[j];
     }
     if (threadIdx.x == 0) R[23] = (double)(gtimer() - t_start);
     zero_long(tm, d.kn, d.dg);
-    tm.template publish<24>(R, kMaxMask);
+    tm.template publish<24, kMaxMask>(R);
     if (!tm.sync()) return false;
-    tm.template collect<24>(R, kMaxMask);
+    tm.template collect<24, kMaxMask>(R);
     prim_res = R[0];
     dual_res = R[6] / c;
     obj = (0.5 * R[21] + R[22]) / c;
@@ -931,7 +1062,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   }
   for (int i = tid; i < m; i += nth) {
     const double Ei = d.E[i];
-    d.z_out[i] = z[i] / Ei;
+    d.z_out[i] = z[i] * d.Einv[i];
     d.y_out[i] = Ei * y[i] / c;
     double dv = d.dy[i];
     const uint8_t t = d.rtype[i];

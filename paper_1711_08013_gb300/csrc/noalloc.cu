@@ -86,7 +86,8 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   const size_t tmpn = nkn > na ? nkn : na;
   const size_t ch_kn = nkn / kChunk + nkn / 257 + 1, lr_kn = nkn / 257 + 1;
   const size_t ch_a = na / kChunk + na / 257 + 1, lr_a = na / 257 + 1;
-  size_t o[64];
+  constexpr int kSlots = 96;  // ≥ the number of take() calls below (68)
+  size_t o[kSlots];
   int c = 0;
   o[c++] = L.template take<int>(n + 1);       // 0 kn_rp
   o[c++] = L.template take<int>(nkn);         // 1 kn_ci
@@ -107,19 +108,20 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   o[c++] = L.template take<int4>(ch_a);       // 16 a chunks
   o[c++] = L.template take<int>(lr_a);        // 17 a long rows
   o[c++] = L.template take<uint8_t>(m);       // 18 rtype
-  const int nvec_n = 14, nvec_m = 18;
+  const int nvec_n = 15, nvec_m = 19;
   const int first_n = c;
   for (int k = 0; k < nvec_n; ++k) o[c++] = L.template take<double>(n);
   const int first_m = c;
   for (int k = 0; k < nvec_m; ++k) o[c++] = L.template take<double>(m);
   const int first_tn = c;
-  for (int k = 0; k < 7; ++k) o[c++] = L.template take<T>(n);
+  for (int k = 0; k < 10; ++k) o[c++] = L.template take<T>(n);
   const int at_rt = c;
-  o[c++] = L.template take<T>(m);
+  for (int k = 0; k < 3; ++k) o[c++] = L.template take<T>(m);
   const int at_sc = c;
   o[c++] = L.template take<Scalars>(1);
   const int at_err = c;
   o[c++] = L.template take<int>(2);
+  static_assert(19 + 15 + 19 + 10 + 3 + 2 <= kSlots, "scratch slot table too small");
   if (base && p) {
     Dev<T>& d = p->d;
     d.n = in.n;
@@ -144,14 +146,16 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
     p->a_long = (int*)(base + o[17]);
     d.rtype = (uint8_t*)(base + o[18]);
     double** nv[] = {&d.D, &d.q, &d.pdiag, &d.dg, &d.nrm_n, &d.x, &d.dx, &d.px,
-                     &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt};
+                     &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt, &d.Dinv};
     for (int k = 0; k < nvec_n; ++k) *nv[k] = (double*)(base + o[first_n + k]);
     double** mv[] = {&d.E, &d.l, &d.u, &d.rho, &d.rho_inv, &d.nrm_m, &d.z, &d.y, &d.dy,
-                     &d.ax, &d.adx, &d.azt, &d.z_out, &d.y_out, &d.pcert, &d.zt, &d.wm, &d.um};
+                     &d.ax, &d.adx, &d.azt, &d.z_out, &d.y_out, &d.pcert, &d.zt, &d.wm, &d.um,
+                     &d.Einv};
     for (int k = 0; k < nvec_m; ++k) *mv[k] = (double*)(base + o[first_m + k]);
-    T** tv[] = {&d.dinv, &d.r, &d.b, &d.s, &d.p0, &d.p1, &d.Kp};
-    for (int k = 0; k < 7; ++k) *tv[k] = (T*)(base + o[first_tn + k]);
-    d.rt = (T*)(base + o[at_rt]);
+    T** tv[] = {&d.dinv, &d.b, &d.mr, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1};
+    for (int k = 0; k < 10; ++k) *tv[k] = (T*)(base + o[first_tn + k]);
+    T** tmv[] = {&d.rt0, &d.rt1, &d.ap};
+    for (int k = 0; k < 3; ++k) *tmv[k] = (T*)(base + o[at_rt + k]);
     d.sc = (Scalars*)(base + o[at_sc]);
     p->err = (int*)(base + o[at_err]);
     p->flag = p->err + 1;
@@ -215,7 +219,7 @@ __device__ void build_sched(Sched& S, const int* rp, int nrows, int4* chunks, in
       red[1] += 1.0;
     }
   }
-  block_reduce<2>(red, 0u, sm);
+  block_reduce<2, 0u>(red, sm);
   const double sn = sm[32 * kMaxRed], sc = sm[32 * kMaxRed + 1];
   __syncthreads();
   // long rows and their chunks, in row order, by one thread (few long rows)

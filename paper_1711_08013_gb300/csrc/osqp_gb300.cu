@@ -327,15 +327,16 @@ void fill_dev(osqp_solver* s, Arena& A, Dev<T>& d, int4** kn_ch, int** kn_lr, in
   d.u_raw = A.take<double>(m);
   d.rtype = A.take<uint8_t>(m);
   double** nvec[] = {&d.D, &d.q, &d.pdiag, &d.dg, &d.nrm_n, &d.x, &d.dx, &d.px,
-                     &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt};
+                     &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt, &d.Dinv};
   for (double** p : nvec) *p = A.take<double>(n);
   double** mvec[] = {&d.E, &d.l, &d.u, &d.rho, &d.rho_inv, &d.nrm_m, &d.z, &d.y,
                      &d.dy, &d.ax, &d.adx, &d.azt, &d.z_out, &d.y_out, &d.pcert,
-                     &d.zt, &d.wm, &d.um};
+                     &d.zt, &d.wm, &d.um, &d.Einv};
   for (double** p : mvec) *p = A.take<double>(m);
-  T** tn[] = {&d.dinv, &d.r, &d.b, &d.s, &d.p0, &d.p1, &d.Kp};
+  T** tn[] = {&d.dinv, &d.b, &d.mr, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1};
   for (T** p : tn) *p = A.take<T>(n);
-  d.rt = A.take<T>(m);
+  T** tmv[] = {&d.rt0, &d.rt1, &d.ap};
+  for (T** p : tmv) *p = A.take<T>(m);
   d.kn.nrows = n;
   d.kn.group = s->kn_s.group;
   d.kn.long_thresh = s->kn_s.long_thresh;
@@ -744,6 +745,8 @@ int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const 
                                                             0);
     if (e != cudaSuccess) return fail(OSQP_ERR_CUDA);
     per_sm = std::max(1, std::min(std::min(occ, occ2), std::min(occ3, 2)));
+    // the grid reduction combines at most 512 per-CTA partials
+    while (per_sm > 1 && s->num_sms * per_sm > 512) --per_sm;
   }
   s->grid = s->num_sms * per_sm;
   {
