@@ -38,6 +38,8 @@ WORKLOADS = {
     "random": (0, "random QP n=50 m=500, P=MM^T+1e-2 I, A at 15% N(0,1)"),
     "portfolio": (2, "portfolio QP n=10000 assets k=100 factors, F at 50% N(0,1); "
                      "variables (x,y) n=10100, rows m=10101"),
+    "mpc_batch": (3, "4096 ragged MPC QPs, nx~U{4..32}, nu=nx/2, T~U{10..30}, one persistent "
+                     "launch (cold: scaling + ADMM per problem)"),
 }
 
 
@@ -182,11 +184,148 @@ def cpu_baseline(args, qp):
                       f"{dt:.1f} s, single thread"}
 
 
+def batch_main(args, ws, rank, local):
+    """Batched workload: a step is one cold solve of every problem of the batch
+    (Ruiz scaling + ADMM), timed on the device; the data (≈ GBs) exceed L2."""
+    import torch
+    import torch.distributed as dist
+    from paper_1711_08013_gb300 import _binding as B
+    from paper_1711_08013_gb300.solver import BatchSolver
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    count = int(os.environ.get("OSQP_BATCH_COUNT", "4096"))
+    qps = pb.mpc_batch(count, seed=3000 + 100000 * rank)
+    prec = B.FP64 if args.precision == "fp64" else B.FP32_MIXED
+    stream = torch.cuda.Stream()
+    bs = BatchSolver(qps, stream=stream.cuda_stream, precision=prec)
+    h = bs.handle
+    for _ in range(args.warmup):
+        B.osqp_batch_reset(h)
+        B.osqp_batch_solve(h)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(torch.cuda.current_device())
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    infos = []
+    for k in range(args.steps):
+        B.osqp_batch_reset(h)
+        evs[k][0].record(stream)
+        B.osqp_batch_solve_async(h)
+        evs[k][1].record(stream)
+        stream.synchronize()
+        infos.append([bs.result(i) for i in range(count)] if k == args.steps - 1 else None)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    step_s = [a.elapsed_time(b) * 1e-3 for a, b in evs]
+    total = sum(step_s)
+    last = infos[-1]
+    if any(r.status != B.SOLVED for r in last):
+        raise SystemExit("a batched solve did not converge")
+    iters = sum(r.iter for r in last)
+    lat = sorted(r.solve_time for r in last)
+    n_solves = count * args.steps
+    if ws > 1:
+        t = torch.tensor([total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t[0])
+    sv = 8 if prec == B.FP64 else 4
+    bytes_launch = sum(admm_bytes(q.n, q.m, q.P_full().nnz + q.A.nnz, q.A.nnz, sv, r.iter,
+                                  r.pcg_iters, (r.iter + 24) // 25) for q, r in zip(qps, last))
+    t_launch = statistics.mean(step_s)
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    # end to end through the public API: new q/l/u of every problem from
+    # pinned host memory, the solve, and x, y of every problem back to the host
+    pins = [(torch.tensor(q.q).pin_memory(), torch.tensor(q.l).pin_memory(),
+             torch.tensor(q.u).pin_memory()) for q in qps]
+    outs = [(torch.empty(q.n, dtype=torch.float64).pin_memory(),
+             torch.empty(q.m, dtype=torch.float64).pin_memory()) for q in qps]
+    L = B.lib()
+
+    def e2e_step():
+        for i, (a, b_, c) in enumerate(pins):
+            if L.osqp_batch_update_vectors(h, i, a.data_ptr(), b_.data_ptr(), c.data_ptr()) != 0:
+                raise SystemExit("update failed")
+        B.osqp_batch_solve(h)
+        for i, (xo, yo) in enumerate(outs):
+            if L.osqp_batch_get(h, i, xo.data_ptr(), yo.data_ptr(), None, None) != 0:
+                raise SystemExit("get failed")
+
+    e2e_step()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        B.osqp_batch_reset(h)
+        e2e_step()
+    e2e_dt = time.perf_counter() - t0
+    line = {
+        "metric": METRIC, "value": ws * n_solves / total, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == B.FP64 else "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["mpc_batch"][1].replace("4096", str(count)),
+                   "precision": args.precision, "eps": 1e-3,
+                   "l2": "inputs larger than L2 (no flush)"},
+        "admm_iter_per_s": ws * iters / (total / args.steps),
+        "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[int(0.99 * (len(lat) - 1))],
+        "admm_iters_per_solve": iters / count,
+        "pcg_iters_per_solve": sum(r.pcg_iters for r in last) / count,
+        "roofline": {"bound": "hbm", "kernel": "k_batch", "achieved": bytes_launch / t_launch / 1e9,
+                     "peak": peak, "unit": "GB/s", "frac": bytes_launch / t_launch / 1e9 / peak,
+                     "traffic": None, "algorithmic_bytes_per_launch": bytes_launch},
+        "e2e": {"value": ws * count * e2e_steps / e2e_dt, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * sum(q.n + 2 * q.m for q in qps),
+                "d2h_bytes_per_step": 8 * sum(q.n + q.m for q in qps)},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    bs.close()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline(qps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _oracle_solve_one(qp):
+    from oracle import oracle as O
+    r = O.solve(qp)
+    return r.status
+
+
+def batch_cpu_baseline(qps, sample=256):
+    """The oracle on a bounded sample of the batch, one problem per process
+    across all host cores (spawned pool: safe after CUDA initialisation)."""
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    sub = qps[:: max(1, len(qps) // sample)][:sample]
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_solve_one, sub[:cores])  # warm the workers
+        t0 = time.perf_counter()
+        pool.map(_oracle_solve_one, sub, chunksize=1)
+        dt = time.perf_counter() - t0
+    return {"value": len(sub) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(sub)} of the {len(qps)} batch problems, one per process on "
+                      f"{cores} cores, {dt:.1f} s"}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload == "mpc_batch":
+        return batch_main(args, ws, rank, local)
 
     import torch
     import torch.distributed as dist

@@ -181,6 +181,53 @@ int32_t osqp_get_certificate(osqp_solver* s, double* prim_inf_y, double* dual_in
 /* Release device memory and the solver. */
 int32_t osqp_cleanup(osqp_solver* s);
 
+/* ---- batched solves -------------------------------------------------------
+ * Many independent QPs of the form of Eq. (pb:qp), each with its own sizes
+ * and sparsity, resident on the device together and solved by one persistent
+ * launch: every CTA takes whole problems from a device work counter (largest
+ * first) and runs the complete solve of the single-problem entry points for
+ * them (Alg. 2 scaling, Algorithm 1 with PCG, §3.4/§5.1 termination, §5.2 ρ̄
+ * adaptation).  Problems share no reduction, so a problem's result does not
+ * depend on which other problems are in the batch. */
+typedef struct osqp_batch osqp_batch;
+
+/* count problems; P_upper[i], A[i] (host CSC as for osqp_setup) and
+ * q[i], l[i], u[i] (host arrays).  One device allocation holds everything.
+ * The settings apply to every problem; settings->launch is ignored. */
+int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P_upper,
+                         const double* const* q, const osqp_csc* A, const double* const* l,
+                         const double* const* u, const osqp_settings* settings, void* stream);
+
+/* Solve every problem and wait; problems marked by setup, osqp_batch_reset
+ * or matrix data are scaled first, problems whose vectors changed are
+ * refreshed, all others warm-start from their last iterates (§6) unless
+ * settings->warm_start == 0. */
+int32_t osqp_batch_solve(osqp_batch* b);
+
+/* As osqp_batch_solve without waiting; results are read after the stream
+ * reaches this point (osqp_batch_get waits). */
+int32_t osqp_batch_solve_async(osqp_batch* b);
+
+/* Solve only the k problems listed in idx (distinct indices) and wait. */
+int32_t osqp_batch_solve_subset(osqp_batch* b, const int32_t* idx, int32_t k);
+
+/* Mark every problem for a cold solve: rescale, ρ̄ = ρ̄⁰, zero iterates. */
+int32_t osqp_batch_reset(osqp_batch* b);
+
+/* §6 vectors as parameters for problem i (host arrays, NULL = unchanged);
+ * applied at the next solve, which warm-starts problem i. */
+int32_t osqp_batch_update_vectors(osqp_batch* b, int32_t i, const double* q, const double* l,
+                                  const double* u);
+
+/* Unscaled x (n_i), y (m_i), z (m_i) of problem i (host arrays, any may be
+ * NULL) and its info (solve_time = that problem's device time inside the
+ * last launch, setup_time = the whole launch's device time).  Waits for the
+ * stream. */
+int32_t osqp_batch_get(osqp_batch* b, int32_t i, double* x, double* y, double* z,
+                       osqp_info* info);
+
+int32_t osqp_batch_cleanup(osqp_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

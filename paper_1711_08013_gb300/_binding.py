@@ -75,6 +75,15 @@ _SIGS = {
     "osqp_get_solution_device": (C.c_int32, [_P, _P, _P]),
     "osqp_get_certificate": (C.c_int32, [_P, _P, _P]),
     "osqp_cleanup": (C.c_int32, [_P]),
+    "osqp_batch_setup": (C.c_int32, [C.POINTER(_P), C.c_int32, _P, _P, _P, _P, _P,
+                                     C.POINTER(osqp_settings), _P]),
+    "osqp_batch_solve": (C.c_int32, [_P]),
+    "osqp_batch_solve_async": (C.c_int32, [_P]),
+    "osqp_batch_solve_subset": (C.c_int32, [_P, _P, C.c_int32]),
+    "osqp_batch_reset": (C.c_int32, [_P]),
+    "osqp_batch_update_vectors": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
+    "osqp_batch_get": (C.c_int32, [_P, C.c_int32, _P, _P, _P, C.POINTER(osqp_info)]),
+    "osqp_batch_cleanup": (C.c_int32, [_P]),
 }
 
 
@@ -211,3 +220,63 @@ def osqp_get_certificate(h, n: int, m: int):
 def osqp_cleanup(h):
     if h:
         _check(lib().osqp_cleanup(h), "osqp_cleanup")
+
+
+# ---------------------------------------------------------------------------
+# batched solves
+# ---------------------------------------------------------------------------
+def osqp_batch_setup(qps, settings: osqp_settings, stream: int | None = None):
+    """qps: sequence of objects with P (upper CSC), q, A (CSC), l, u."""
+    count = len(qps)
+    keep = []
+    Ps = (osqp_csc * count)()
+    As = (osqp_csc * count)()
+    qv, lv, uv = (C.c_void_p * count)(), (C.c_void_p * count)(), (C.c_void_p * count)()
+    for i, qp in enumerate(qps):
+        Ps[i] = _csc(qp.P, keep)
+        As[i] = _csc(qp.A, keep)
+        arrs = [np.ascontiguousarray(v, np.float64) for v in (qp.q, qp.l, qp.u)]
+        keep += arrs
+        qv[i], lv[i], uv[i] = (_ptr(a) for a in arrs)
+    h = C.c_void_p()
+    rc = lib().osqp_batch_setup(C.byref(h), count, C.cast(Ps, C.c_void_p), C.cast(qv, C.c_void_p),
+                                C.cast(As, C.c_void_p), C.cast(lv, C.c_void_p),
+                                C.cast(uv, C.c_void_p), C.byref(settings), stream)
+    _check(rc, "osqp_batch_setup")
+    return h.value
+
+
+def osqp_batch_solve(h):
+    _check(lib().osqp_batch_solve(h), "osqp_batch_solve")
+
+
+def osqp_batch_solve_async(h):
+    _check(lib().osqp_batch_solve_async(h), "osqp_batch_solve_async")
+
+
+def osqp_batch_solve_subset(h, idx):
+    a = np.ascontiguousarray(idx, np.int32)
+    _check(lib().osqp_batch_solve_subset(h, _ptr(a), int(a.size)), "osqp_batch_solve_subset")
+
+
+def osqp_batch_reset(h):
+    _check(lib().osqp_batch_reset(h), "osqp_batch_reset")
+
+
+def osqp_batch_update_vectors(h, i, q=None, l=None, u=None):
+    arrs = [None if v is None else np.ascontiguousarray(v, np.float64) for v in (q, l, u)]
+    _check(lib().osqp_batch_update_vectors(h, int(i), *[_ptr(a) for a in arrs]),
+           "osqp_batch_update_vectors")
+
+
+def osqp_batch_get(h, i, n, m):
+    x, y, z = np.empty(n), np.empty(m), np.empty(m)
+    info = osqp_info()
+    _check(lib().osqp_batch_get(h, int(i), _ptr(x), _ptr(y), _ptr(z), C.byref(info)),
+           "osqp_batch_get")
+    return x, y, z, info
+
+
+def osqp_batch_cleanup(h):
+    if h:
+        _check(lib().osqp_batch_cleanup(h), "osqp_batch_cleanup")

@@ -1,0 +1,571 @@
+// Batched solve of many independent QPs in one persistent launch.
+//
+// Every problem keeps its own sizes, sparsity pattern, scaling, ρ̄ and
+// iterates resident in one device allocation.  k_batch runs a grid of
+// persistent CTAs (two per SM); each CTA takes the next problem from a device
+// work counter — problems are queued largest first — and runs the whole
+// solve for it with the one-CTA team: Ruiz scaling or a vector refresh when
+// requested, then Algorithm 1 with PCG, termination and unscaling.  Problems
+// never share a reduction, so each result is bit-for-bit the same whether
+// the problem is solved alone or among others.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/osqp_gb300.h"
+#include "device.cuh"
+#include "host_common.h"
+
+using namespace osqpgb;
+using namespace osqpgb::host;
+
+namespace {
+
+constexpr int kBatchThreads = 256;
+constexpr long long kBatchWarps = kBatchThreads / 32;
+
+enum : int { kModeScale = 1, kModeRefresh = 2, kModeReset = 4 };
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads, 2)
+    k_batch(const Dev<T>* __restrict__ devs, const int* __restrict__ order, int count,
+            const __grid_constant__ Params P, const int* __restrict__ mode, int* queue,
+            unsigned long long* times) {
+  __shared__ double sm[kSmemDoubles];
+  __shared__ int sidx;
+  BlockTeam tm{sm};
+  for (;;) {
+    if (threadIdx.x == 0) sidx = atomicAdd(queue, 1);
+    __syncthreads();
+    const int idx = sidx;
+    __syncthreads();
+    if (idx >= count) break;
+    const int p = order[idx];
+    const Dev<T>& d = devs[p];
+    const unsigned long long t0 = gtimer();
+    const int md = mode[p];
+    const double rho_bar = d.sc->rho_bar;
+    if (md & kModeScale) {
+      scale_stage(tm, d, P, rho_bar, true);
+    } else {
+      if (md & kModeRefresh) refresh_stage(tm, d, P, rho_bar);
+      if (md & kModeReset) {
+        for (int j = threadIdx.x; j < d.n; j += blockDim.x) {
+          d.x[j] = 0.0;
+          d.dx[j] = 0.0;
+          d.xt[j] = 0.0;
+        }
+        for (int i = threadIdx.x; i < d.m; i += blockDim.x) {
+          d.z[i] = 0.0;
+          d.y[i] = 0.0;
+          d.dy[i] = 0.0;
+          d.zt[i] = 0.0;
+        }
+        __syncthreads();
+      }
+    }
+    admm_stage(tm, d, P);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      times[2 * p] = t0;
+      times[2 * p + 1] = gtimer();
+    }
+  }
+}
+
+// Per-problem sizes and offsets.
+struct ProblemLayout {
+  int n = 0, m = 0, nnz_kn = 0, nnz_a = 0;
+  SchedHost kn_s, a_s;
+  size_t s_off = 0;  // offset of this problem's static block
+  size_t v_off = 0;  // offset of this problem's dynamic block
+};
+
+struct Bump {
+  size_t off = 0;
+  template <typename V>
+  size_t take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t at = off;
+    off += std::max<size_t>(count, 1) * sizeof(V);
+    return at;
+  }
+};
+
+// Static block (uploaded once): structure, raw values, schedules, raw vectors.
+struct StaticOffsets {
+  size_t kn_rp, kn_ci, kn_raw, a_rp, a_ci, a_raw, kn_ch, kn_lr, a_ch, a_lr, q, l, u, end;
+};
+
+StaticOffsets static_offsets(const ProblemLayout& L) {
+  Bump b;
+  StaticOffsets o;
+  o.kn_rp = b.take<int>(L.n + 1);
+  o.kn_ci = b.take<int>(L.nnz_kn);
+  o.kn_raw = b.take<double>(L.nnz_kn);
+  o.a_rp = b.take<int>(L.m + 1);
+  o.a_ci = b.take<int>(L.nnz_a);
+  o.a_raw = b.take<double>(L.nnz_a);
+  o.kn_ch = b.take<int4>(L.kn_s.chunks.size());
+  o.kn_lr = b.take<int>(L.kn_s.long_rows.size());
+  o.a_ch = b.take<int4>(L.a_s.chunks.size());
+  o.a_lr = b.take<int>(L.a_s.long_rows.size());
+  o.q = b.take<double>(L.n);
+  o.l = b.take<double>(L.m);
+  o.u = b.take<double>(L.m);
+  o.end = (b.off + 255) & ~(size_t)255;
+  return o;
+}
+
+// Dynamic block: working matrices and every vector of Dev<T>.
+template <typename T>
+size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
+  Bump b;
+  const size_t n = L.n, m = L.m;
+  const size_t kn_v = b.take<T>(L.nnz_kn);
+  const size_t a_v = b.take<T>(L.nnz_a);
+  const size_t rt = b.take<uint8_t>(m);
+  size_t on[15], om[19], otn[10], otm[3];
+  for (auto& v : on) v = b.take<double>(n);
+  for (auto& v : om) v = b.take<double>(m);
+  for (auto& v : otn) v = b.take<T>(n);
+  for (auto& v : otm) v = b.take<T>(m);
+  const size_t sc = b.take<Scalars>(1);
+  if (base && d) {
+    d->kn_v = (T*)(base + kn_v);
+    d->a_v = (T*)(base + a_v);
+    d->rtype = (uint8_t*)(base + rt);
+    double** nv[] = {&d->D, &d->q, &d->pdiag, &d->dg, &d->nrm_n, &d->x, &d->dx, &d->px,
+                     &d->aty, &d->pdx, &d->atdy, &d->x_out, &d->dcert, &d->xt, &d->Dinv};
+    for (int k = 0; k < 15; ++k) *nv[k] = (double*)(base + on[k]);
+    double** mv[] = {&d->E, &d->l, &d->u, &d->rho, &d->rho_inv, &d->nrm_m, &d->z, &d->y,
+                     &d->dy, &d->ax, &d->adx, &d->azt, &d->z_out, &d->y_out, &d->pcert,
+                     &d->zt, &d->wm, &d->um, &d->Einv};
+    for (int k = 0; k < 19; ++k) *mv[k] = (double*)(base + om[k]);
+    T** tn[] = {&d->dinv, &d->b, &d->mr, &d->p, &d->r0, &d->r1, &d->s0, &d->s1, &d->w0, &d->w1};
+    for (int k = 0; k < 10; ++k) *tn[k] = (T*)(base + otn[k]);
+    T** tmv[] = {&d->rt0, &d->rt1, &d->ap};
+    for (int k = 0; k < 3; ++k) *tmv[k] = (T*)(base + otm[k]);
+    d->sc = (Scalars*)(base + sc);
+  }
+  return (b.off + 255) & ~(size_t)255;
+}
+
+}  // namespace
+
+struct osqp_batch {
+  int count = 0, device = 0, num_sms = 0, grid = 0;
+  cudaStream_t stream = nullptr;
+  osqp_settings set{};
+  Params P{};
+  std::vector<ProblemLayout> L;
+  std::vector<int> order;           // problems sorted by work, largest first
+  std::vector<int> mode;            // per-problem kernel mode for the next launch
+  std::vector<Scalars> sc_host;     // scalars after the last solve
+  std::vector<unsigned long long> times_host;
+  char* arena = nullptr;
+  size_t static_bytes = 0, arena_bytes = 0;
+  void* devs = nullptr;             // Dev<T>[count]
+  std::vector<char> devs_host;      // host copy of the Dev<T> array
+  int* order_d = nullptr;
+  int* mode_d = nullptr;
+  int* queue = nullptr;
+  unsigned long long* times_d = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double last_time = 0.0;
+  bool solved = false;
+  bool dirty = false;  // a launch has not been collected into sc_host yet
+};
+
+namespace {
+
+template <typename T>
+Dev<T>* dev_at(osqp_batch* b, int i) {
+  return reinterpret_cast<Dev<T>*>(b->devs_host.data()) + i;
+}
+
+template <typename T>
+void fill_batch_devs(osqp_batch* b) {
+  b->devs_host.assign(sizeof(Dev<T>) * b->count, 0);
+  for (int i = 0; i < b->count; ++i) {
+    const ProblemLayout& L = b->L[i];
+    Dev<T>* d = dev_at<T>(b, i);
+    std::memset((void*)d, 0, sizeof(Dev<T>));
+    const StaticOffsets o = static_offsets(L);
+    char* sb = b->arena + L.s_off;
+    d->n = L.n;
+    d->m = L.m;
+    d->kn_rp = (const int*)(sb + o.kn_rp);
+    d->kn_ci = (const int*)(sb + o.kn_ci);
+    d->kn_raw = (const double*)(sb + o.kn_raw);
+    d->a_rp = (const int*)(sb + o.a_rp);
+    d->a_ci = (const int*)(sb + o.a_ci);
+    d->a_raw = (const double*)(sb + o.a_raw);
+    d->q_raw = (const double*)(sb + o.q);
+    d->l_raw = (const double*)(sb + o.l);
+    d->u_raw = (const double*)(sb + o.u);
+    d->kn = Sched{L.n, L.kn_s.group, L.kn_s.long_thresh, (int)L.kn_s.chunks.size(),
+                  (int)L.kn_s.long_rows.size(), (const int4*)(sb + o.kn_ch),
+                  (const int*)(sb + o.kn_lr)};
+    d->as = Sched{L.m, L.a_s.group, L.a_s.long_thresh, (int)L.a_s.chunks.size(),
+                  (int)L.a_s.long_rows.size(), (const int4*)(sb + o.a_ch),
+                  (const int*)(sb + o.a_lr)};
+    dynamic_carve<T>(L, b->arena + L.v_off, d);
+  }
+}
+
+template <typename T>
+int launch_batch(osqp_batch* b, const int* order_d, int count) {
+  if (cudaMemcpyAsync(b->mode_d, b->mode.data(), sizeof(int) * b->count, cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
+  const int grid = std::max(1, std::min(b->grid, count));
+  k_batch<T><<<grid, kBatchThreads, 0, b->stream>>>((const Dev<T>*)b->devs, order_d, count, b->P,
+                                                     b->mode_d, b->queue, b->times_d);
+  return cudaGetLastError() == cudaSuccess ? OSQP_OK : OSQP_ERR_CUDA;
+}
+
+int batch_launch(osqp_batch* b, const int* order_d, int count) {
+  if (cudaEventRecord(b->ev[0], b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
+  const int rc = b->set.precision == OSQP_PRECISION_FP64 ? launch_batch<double>(b, order_d, count)
+                                                         : launch_batch<float>(b, order_d, count);
+  if (rc) return rc;
+  if (cudaEventRecord(b->ev[1], b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
+  b->solved = true;
+  b->dirty = true;
+  return OSQP_OK;
+}
+
+int batch_collect(osqp_batch* b) {
+  // Scalars of every problem (they sit at the same offset in each dynamic block).
+  for (int i = 0; i < b->count; ++i) {
+    const Scalars* src = b->set.precision == OSQP_PRECISION_FP64 ? dev_at<double>(b, i)->sc
+                                                                 : dev_at<float>(b, i)->sc;
+    if (cudaMemcpyAsync(&b->sc_host[i], src, sizeof(Scalars), cudaMemcpyDeviceToHost, b->stream) !=
+        cudaSuccess)
+      return OSQP_ERR_CUDA;
+  }
+  if (cudaMemcpyAsync(b->times_host.data(), b->times_d, sizeof(unsigned long long) * 2 * b->count,
+                      cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
+  float ms = 0.f;
+  if (b->solved && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess)
+    b->last_time = ms * 1e-3;
+  b->dirty = false;
+  return OSQP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, const double* const* q,
+                         const osqp_csc* A, const double* const* l, const double* const* u,
+                         const osqp_settings* settings, void* stream) {
+  if (!out || !P || !A || !q || !settings || count < 1) return OSQP_ERR_ARG;
+  *out = nullptr;
+  int rc = check_settings(*settings);
+  if (rc) return rc;
+  for (int i = 0; i < count; ++i) {
+    const int n = P[i].n_cols, m = A[i].n_rows;
+    if (n < 1 || m < 0 || P[i].n_rows != n || A[i].n_cols != n) return OSQP_ERR_DIMS;
+    if (!q[i] || (m > 0 && (!l || !u || !l[i] || !u[i]))) return OSQP_ERR_ARG;
+    if (!valid_csc(&P[i], n, n, true) || !valid_csc(&A[i], m, n, false)) return OSQP_ERR_CSC;
+    if (!finite_all(P[i].val, P[i].nnz) || !finite_all(A[i].val, A[i].nnz) || !finite_all(q[i], n))
+      return OSQP_ERR_NONFINITE;
+    for (int r = 0; r < m; ++r) {
+      if (std::isnan(l[i][r]) || std::isnan(u[i][r])) return OSQP_ERR_NONFINITE;
+      if (l[i][r] > u[i][r]) return OSQP_ERR_LGTU;
+    }
+  }
+  osqp_batch* b = new (std::nothrow) osqp_batch();
+  if (!b) return OSQP_ERR_OOM;
+  auto fail = [&](int code) {
+    osqp_batch_cleanup(b);
+    return code;
+  };
+  b->count = count;
+  b->set = *settings;
+  b->P = make_params(*settings);
+  b->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&b->device) != cudaSuccess) return fail(OSQP_ERR_CUDA);
+  if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+    return fail(OSQP_ERR_CUDA);
+  int occ = 0;
+  cudaError_t e = settings->precision == OSQP_PRECISION_FP64
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<double>,
+                                                                      kBatchThreads, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<float>,
+                                                                      kBatchThreads, 0);
+  if (e != cudaSuccess) return fail(OSQP_ERR_CUDA);
+  b->grid = b->num_sms * std::max(1, occ);
+
+  // Structure of every problem, its schedule and its place in the arena:
+  // all static blocks first (one upload), then all dynamic blocks.
+  std::vector<HostStructure> hs(count);
+  b->L.resize(count);
+  size_t s_total = 0;
+  for (int i = 0; i < count; ++i) {
+    build_host_structure(&P[i], &A[i], &hs[i]);
+    ProblemLayout& L = b->L[i];
+    L.n = hs[i].n;
+    L.m = hs[i].m;
+    L.nnz_kn = hs[i].nnz_kn;
+    L.nnz_a = hs[i].nnz_a;
+    L.kn_s = make_sched(hs[i].kn_rp, kBatchWarps);
+    L.a_s = make_sched(hs[i].a_rp, kBatchWarps);
+    L.s_off = s_total;
+    s_total += static_offsets(L).end;
+  }
+  b->static_bytes = s_total;
+  size_t v_total = s_total;
+  for (int i = 0; i < count; ++i) {
+    b->L[i].v_off = v_total;
+    v_total += settings->precision == OSQP_PRECISION_FP64
+                   ? dynamic_carve<double>(b->L[i], nullptr, nullptr)
+                   : dynamic_carve<float>(b->L[i], nullptr, nullptr);
+  }
+  b->arena_bytes = v_total;
+  const size_t dev_bytes = (settings->precision == OSQP_PRECISION_FP64 ? sizeof(Dev<double>)
+                                                                       : sizeof(Dev<float>)) *
+                           (size_t)count;
+  e = cudaMalloc((void**)&b->arena, b->arena_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b->arena = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? OSQP_ERR_OOM : OSQP_ERR_CUDA);
+  }
+  if (cudaMalloc(&b->devs, dev_bytes) != cudaSuccess ||
+      cudaMalloc((void**)&b->order_d, sizeof(int) * count) != cudaSuccess ||
+      cudaMalloc((void**)&b->mode_d, sizeof(int) * count) != cudaSuccess ||
+      cudaMalloc((void**)&b->queue, sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&b->times_d, sizeof(unsigned long long) * 2 * count) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(OSQP_ERR_OOM);
+  }
+  for (auto& ev : b->ev)
+    if (cudaEventCreate(&ev) != cudaSuccess) return fail(OSQP_ERR_CUDA);
+
+  // Upload the static blocks in chunks of at most 256 MB of host staging.
+  const size_t kChunkBytes = (size_t)256 << 20;
+  std::vector<char> stage;
+  size_t chunk_begin = 0;
+  auto flush = [&](size_t upto) -> bool {
+    if (upto <= chunk_begin) return true;
+    if (cudaMemcpy(b->arena + chunk_begin, stage.data(), upto - chunk_begin,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return false;
+    chunk_begin = upto;
+    stage.clear();
+    return true;
+  };
+  for (int i = 0; i < count; ++i) {
+    const ProblemLayout& L = b->L[i];
+    const StaticOffsets o = static_offsets(L);
+    if (L.s_off + o.end - chunk_begin > kChunkBytes && !flush(L.s_off)) return fail(OSQP_ERR_CUDA);
+    stage.resize(L.s_off + o.end - chunk_begin, 0);
+    char* base = stage.data() + (L.s_off - chunk_begin);
+    const HostStructure& h = hs[i];
+    auto put = [&](size_t off, const void* src, size_t bytes) {
+      if (bytes) std::memcpy(base + off, src, bytes);
+    };
+    put(o.kn_rp, h.kn_rp.data(), sizeof(int) * h.kn_rp.size());
+    put(o.kn_ci, h.kn_ci.data(), sizeof(int) * h.kn_ci.size());
+    put(o.a_rp, h.a_rp.data(), sizeof(int) * h.a_rp.size());
+    put(o.a_ci, h.a_ci.data(), sizeof(int) * h.a_ci.size());
+    double* knr = reinterpret_cast<double*>(base + o.kn_raw);
+    for (int k = 0; k < h.nnz_kn; ++k) {
+      const int src = h.kn_src[k];
+      knr[k] = src < h.nnz_p ? P[i].val[src] : A[i].val[src - h.nnz_p];
+    }
+    double* ar = reinterpret_cast<double*>(base + o.a_raw);
+    for (int k = 0; k < h.nnz_a; ++k) ar[k] = A[i].val[h.a_src[k] - h.nnz_p];
+    put(o.kn_ch, L.kn_s.chunks.data(), sizeof(int4) * L.kn_s.chunks.size());
+    put(o.kn_lr, L.kn_s.long_rows.data(), sizeof(int) * L.kn_s.long_rows.size());
+    put(o.a_ch, L.a_s.chunks.data(), sizeof(int4) * L.a_s.chunks.size());
+    put(o.a_lr, L.a_s.long_rows.data(), sizeof(int) * L.a_s.long_rows.size());
+    put(o.q, q[i], sizeof(double) * L.n);
+    if (L.m) {
+      put(o.l, l[i], sizeof(double) * L.m);
+      put(o.u, u[i], sizeof(double) * L.m);
+    }
+    hs[i] = HostStructure();  // release host memory early
+  }
+  if (!flush(b->static_bytes)) return fail(OSQP_ERR_CUDA);
+
+  if (settings->precision == OSQP_PRECISION_FP64) fill_batch_devs<double>(b);
+  else fill_batch_devs<float>(b);
+  if (cudaMemcpy(b->devs, b->devs_host.data(), dev_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(OSQP_ERR_CUDA);
+  // Scalars: ρ̄⁰ for every problem; the first launch scales every problem.
+  b->sc_host.assign(count, Scalars{});
+  for (int i = 0; i < count; ++i) b->sc_host[i].rho_bar = settings->rho;
+  for (int i = 0; i < count; ++i) {
+    Scalars* dst = settings->precision == OSQP_PRECISION_FP64 ? dev_at<double>(b, i)->sc
+                                                             : dev_at<float>(b, i)->sc;
+    if (cudaMemcpy(dst, &b->sc_host[i], sizeof(Scalars), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(OSQP_ERR_CUDA);
+  }
+  b->mode.assign(count, kModeScale);
+  b->times_host.assign(2 * (size_t)count, 0);
+  // Work order: largest problem first (a longest-processing-time schedule).
+  b->order.resize(count);
+  std::iota(b->order.begin(), b->order.end(), 0);
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) {
+    return (long long)b->L[a].nnz_kn + b->L[a].nnz_a + b->L[a].n + b->L[a].m >
+           (long long)b->L[c].nnz_kn + b->L[c].nnz_a + b->L[c].n + b->L[c].m;
+  });
+  if (cudaMemcpy(b->order_d, b->order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return fail(OSQP_ERR_CUDA);
+  *out = b;
+  return OSQP_OK;
+}
+
+int32_t osqp_batch_solve_async(osqp_batch* b) {
+  if (!b) return OSQP_ERR_ARG;
+  if (!b->set.warm_start)
+    for (int i = 0; i < b->count; ++i) b->mode[i] |= kModeReset;
+  const int rc = batch_launch(b, b->order_d, b->count);
+  if (rc) return rc;
+  std::fill(b->mode.begin(), b->mode.end(), 0);
+  return OSQP_OK;
+}
+
+int32_t osqp_batch_solve(osqp_batch* b) {
+  const int rc = osqp_batch_solve_async(b);
+  if (rc) return rc;
+  return batch_collect(b);
+}
+
+int32_t osqp_batch_solve_subset(osqp_batch* b, const int32_t* idx, int32_t k) {
+  if (!b || (k > 0 && !idx) || k < 0 || k > b->count) return OSQP_ERR_ARG;
+  if (k == 0) return OSQP_OK;
+  std::vector<int> sel(idx, idx + k);
+  for (int v : sel)
+    if (v < 0 || v >= b->count) return OSQP_ERR_ARG;
+  std::stable_sort(sel.begin(), sel.end(), [&](int a, int c) {
+    return (long long)b->L[a].nnz_kn + b->L[a].nnz_a > (long long)b->L[c].nnz_kn + b->L[c].nnz_a;
+  });
+  if (!b->set.warm_start)
+    for (int v : sel) b->mode[v] |= kModeReset;
+  // the subset takes the front of the order buffer for this launch
+  if (cudaMemcpyAsync(b->order_d, sel.data(), sizeof(int) * k, cudaMemcpyHostToDevice, b->stream) !=
+      cudaSuccess)
+    return OSQP_ERR_CUDA;
+  int rc = batch_launch(b, b->order_d, k);
+  if (rc) return rc;
+  for (int v : sel) b->mode[v] = 0;
+  // restore the full order for the next whole-batch launch
+  if (cudaMemcpyAsync(b->order_d, b->order.data(), sizeof(int) * b->count, cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  return batch_collect(b);
+}
+
+int32_t osqp_batch_reset(osqp_batch* b) {
+  if (!b) return OSQP_ERR_ARG;
+  std::fill(b->mode.begin(), b->mode.end(), (int)kModeScale);
+  for (int i = 0; i < b->count; ++i) b->sc_host[i].rho_bar = b->set.rho;
+  for (int i = 0; i < b->count; ++i) {
+    Scalars* dst = b->set.precision == OSQP_PRECISION_FP64 ? dev_at<double>(b, i)->sc
+                                                          : dev_at<float>(b, i)->sc;
+    if (cudaMemcpyAsync(&dst->rho_bar, &b->set.rho, sizeof(double), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess)
+      return OSQP_ERR_CUDA;
+  }
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? OSQP_OK : OSQP_ERR_CUDA;
+}
+
+int32_t osqp_batch_update_vectors(osqp_batch* b, int32_t i, const double* q, const double* l,
+                                  const double* u) {
+  if (!b || i < 0 || i >= b->count) return OSQP_ERR_ARG;
+  const ProblemLayout& L = b->L[i];
+  if (q && !finite_all(q, L.n)) return OSQP_ERR_NONFINITE;
+  const StaticOffsets o = static_offsets(L);
+  char* sb = b->arena + L.s_off;
+  if (l || u) {
+    std::vector<double> lh(L.m), uh(L.m);
+    if (!l && L.m &&
+        cudaMemcpyAsync(lh.data(), sb + o.l, sizeof(double) * L.m, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+      return OSQP_ERR_CUDA;
+    if (!u && L.m &&
+        cudaMemcpyAsync(uh.data(), sb + o.u, sizeof(double) * L.m, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+      return OSQP_ERR_CUDA;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
+    const double* Lv = l ? l : lh.data();
+    const double* Uv = u ? u : uh.data();
+    for (int r = 0; r < L.m; ++r) {
+      if (std::isnan(Lv[r]) || std::isnan(Uv[r])) return OSQP_ERR_NONFINITE;
+      if (Lv[r] > Uv[r]) return OSQP_ERR_LGTU;
+    }
+  }
+  if (q && cudaMemcpyAsync(sb + o.q, q, sizeof(double) * L.n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (l && L.m && cudaMemcpyAsync(sb + o.l, l, sizeof(double) * L.m, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (u && L.m && cudaMemcpyAsync(sb + o.u, u, sizeof(double) * L.m, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (!(b->mode[i] & kModeScale)) b->mode[i] |= kModeRefresh;
+  return OSQP_OK;
+}
+
+int32_t osqp_batch_get(osqp_batch* b, int32_t i, double* x, double* y, double* z,
+                       osqp_info* info) {
+  if (!b || i < 0 || i >= b->count) return OSQP_ERR_ARG;
+  const ProblemLayout& L = b->L[i];
+  const bool f64 = b->set.precision == OSQP_PRECISION_FP64;
+  const double* xo = f64 ? dev_at<double>(b, i)->x_out : dev_at<float>(b, i)->x_out;
+  const double* yo = f64 ? dev_at<double>(b, i)->y_out : dev_at<float>(b, i)->y_out;
+  const double* zo = f64 ? dev_at<double>(b, i)->z_out : dev_at<float>(b, i)->z_out;
+  if (z && L.m && cudaMemcpyAsync(z, zo, sizeof(double) * L.m, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (x && cudaMemcpyAsync(x, xo, sizeof(double) * L.n, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (y && L.m && cudaMemcpyAsync(y, yo, sizeof(double) * L.m, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
+  if (info) {
+    if (b->dirty) {
+      const int rc = batch_collect(b);
+      if (rc) return rc;
+    }
+    const Scalars& s = b->sc_host[i];
+    std::memset(info, 0, sizeof(*info));
+    info->status = s.status;
+    info->iter = s.iter;
+    info->pcg_iters = s.pcg_iters;
+    info->rho_updates = s.rho_updates;
+    info->ruiz_passes = s.ruiz_passes;
+    info->launch = 1;
+    info->obj_val = s.obj;
+    info->prim_res = s.prim_res;
+    info->dual_res = s.dual_res;
+    info->rho_estimate = s.rho_bar;
+    const unsigned long long t0 = b->times_host[2 * (size_t)i], t1 = b->times_host[2 * (size_t)i + 1];
+    info->solve_time = t1 > t0 ? (double)(t1 - t0) * 1e-9 : 0.0;
+    info->setup_time = b->last_time;  // whole-launch device time
+  }
+  return OSQP_OK;
+}
+
+int32_t osqp_batch_cleanup(osqp_batch* b) {
+  if (!b) return OSQP_ERR_ARG;
+  int rc = OSQP_OK;
+  if (b->arena && cudaStreamSynchronize(b->stream) != cudaSuccess) rc = OSQP_ERR_CUDA;
+  void* ptrs[] = {b->arena, b->devs, b->order_d, b->mode_d, b->queue, b->times_d};
+  for (void* p : ptrs)
+    if (p && cudaFree(p) != cudaSuccess) rc = OSQP_ERR_CUDA;
+  for (auto& ev : b->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete b;
+  return rc;
+}
+
+}  // extern "C"

@@ -75,3 +75,48 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class BatchSolver:
+    """Many independent QPs resident on the GPU, solved by one persistent launch."""
+
+    def __init__(self, qps, stream: int | None = None, **settings):
+        self.sizes = [(qp.P.shape[0], qp.A.shape[0]) for qp in qps]
+        self.settings = B.osqp_set_default_settings(**settings)
+        self.handle = B.osqp_batch_setup(qps, self.settings, stream)
+
+    def solve(self, subset=None):
+        if subset is None:
+            B.osqp_batch_solve(self.handle)
+        else:
+            B.osqp_batch_solve_subset(self.handle, subset)
+
+    def reset(self):
+        B.osqp_batch_reset(self.handle)
+
+    def update_vectors(self, i, q=None, l=None, u=None):
+        B.osqp_batch_update_vectors(self.handle, i, q, l, u)
+
+    def result(self, i) -> Result:
+        n, m = self.sizes[i]
+        x, y, z, info = B.osqp_batch_get(self.handle, i, n, m)
+        return Result(x, y, z, info.status, info.iter, info.pcg_iters, info.rho_updates,
+                      info.obj_val, info.prim_res, info.dual_res, info.rho_estimate,
+                      info.setup_time, info.solve_time, info.launch)
+
+    def close(self):
+        if self.handle:
+            B.osqp_batch_cleanup(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

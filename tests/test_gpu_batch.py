@@ -1,0 +1,137 @@
+"""Batched solves through the C ABI: every problem of a ragged batch against
+the oracle, and each result identical alone and among other problems."""
+import numpy as np
+import pytest
+
+from paper_1711_08013_gb300 import _binding as B
+from paper_1711_08013_gb300 import problems as pb
+from tests.kkt_check import acceptance, objective, objective_interval
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1711_08013_gb300.solver import BatchSolver, Solver  # noqa: E402
+
+HIGH_ORACLE = dict(eps_abs=1e-9, eps_rel=1e-9, max_iter=400000, check_interval=10)
+
+
+def mixed_batch():
+    qps = pb.mpc_batch(12, seed=3100, nx_range=(4, 12), T_range=(5, 12))
+    qps += [pb.random_qp(30, 150, seed=3201), pb.portfolio(3, seed=3202), pb.lasso(5, seed=3203),
+            pb.huber(4, seed=3204), pb.box_qp(25, seed=3205)]
+    return qps
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
+def test_batch_against_oracle(oracle_mod, precision):
+    qps = mixed_batch()
+    with BatchSolver(qps, precision=precision) as bs:
+        bs.solve()
+        res = [bs.result(i) for i in range(len(qps))]
+    for qp, g in zip(qps, res):
+        star = oracle_mod.solve(qp, **HIGH_ORACLE)
+        assert g.status == B.SOLVED, (qp.name, g.status, g.iter)
+        prim, dual, ep, ed = acceptance(qp, g.x, g.y, 1e-3, 1e-3)
+        assert prim <= ep * 1.01 and dual <= ed * 1.01, (qp.name, prim, ep, dual, ed)
+        lo, hi = objective_interval(qp, g.x, g.z, g.y, star.x, star.y)
+        d = objective(qp, g.x) - star.obj_val
+        assert abs(g.obj_val - objective(qp, g.x)) <= 1e-6 * max(1.0, abs(g.obj_val))
+        slack = 1e-7 * max(1.0, abs(star.obj_val))
+        assert lo - slack <= d <= hi + slack, (qp.name, lo, d, hi)
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
+def test_batch_result_same_alone_and_in_mix(precision):
+    qps = mixed_batch()
+    with BatchSolver(qps, precision=precision) as bs:
+        bs.solve()
+        mix = [bs.result(i) for i in range(len(qps))]
+    # MPC problems have no row above the long-row threshold: their arithmetic
+    # order is fixed and the results are bit-identical.  The portfolio has a
+    # 300-entry row whose chunk partials are added atomically, so only
+    # rounding-level agreement holds there.
+    for i, exact in ((0, True), (5, True), (len(qps) - 4, False), (len(qps) - 1, True)):
+        with BatchSolver([qps[i]], precision=precision) as one:
+            one.solve()
+            alone = one.result(0)
+        assert alone.status == mix[i].status
+        if exact:
+            assert alone.iter == mix[i].iter
+            assert np.array_equal(alone.x, mix[i].x), qps[i].name
+            assert np.array_equal(alone.y, mix[i].y), qps[i].name
+        else:
+            tol = 1e-4 if precision == B.FP32_MIXED else 1e-8
+            assert np.allclose(alone.x, mix[i].x, rtol=tol, atol=tol), qps[i].name
+
+
+def test_batch_matches_single_problem_solver(oracle_mod):
+    """The batch kernel and the single-problem one-CTA solver run the same
+    stages; with exact linear solves their iterates agree to rounding."""
+    qps = mixed_batch()[:6]
+    step = dict(adaptive_rho=0, eps_abs=0.0, eps_rel=0.0, eps_pinf=1e-300, eps_dinf=1e-300,
+                pcg_tol_fraction=0.0, pcg_tol_floor=1e-14, pcg_max_iter=2000, check_interval=1,
+                max_iter=30)
+    with BatchSolver(qps, **step) as bs:
+        bs.solve()
+        for i, qp in enumerate(qps):
+            g = bs.result(i)
+            o = oracle_mod.solve(qp, adaptive_rho=0, eps_abs=0.0, eps_rel=0.0, eps_pinf=1e-300,
+                                 eps_dinf=1e-300, check_interval=1, max_iter=30)
+            scale = max(1.0, np.max(np.abs(o.x)))
+            assert np.max(np.abs(g.x - o.x)) <= 1e-8 * scale, qp.name
+
+
+def test_batch_update_vectors_subset_and_warm_start(oracle_mod):
+    qps = mixed_batch()
+    rng = np.random.default_rng(7)
+    with BatchSolver(qps) as bs:
+        bs.solve()
+        first = [bs.result(i) for i in range(len(qps))]
+        pick = [1, 4, len(qps) - 5]
+        new = {}
+        for i in pick:
+            q2, l2, u2 = pb.perturb_vectors(rng, qps[i])
+            new[i] = pb._finish("upd", qps[i].P, q2, qps[i].A, l2, u2)
+            bs.update_vectors(i, q2, l2, u2)
+        bs.solve(subset=pick)
+        for i in pick:
+            g = bs.result(i)
+            qp2 = new[i]
+            assert g.status == B.SOLVED
+            prim, dual, ep, ed = acceptance(qp2, g.x, g.y, 1e-3, 1e-3)
+            assert prim <= ep * 1.01 and dual <= ed * 1.01
+        # problems outside the subset were not touched
+        other = 0
+        g = bs.result(other)
+        assert np.array_equal(g.x, first[other].x)
+        # a warm re-solve of an unchanged problem terminates at the first check
+        bs.solve(subset=[other])
+        assert bs.result(other).iter <= 25
+
+
+def test_batch_reset_reproduces_cold_solve():
+    qps = mixed_batch()[:5]
+    with BatchSolver(qps) as bs:
+        bs.solve()
+        a = [bs.result(i) for i in range(len(qps))]
+        bs.reset()
+        bs.solve()
+        b = [bs.result(i) for i in range(len(qps))]
+    for ra, rb in zip(a, b):
+        assert ra.iter == rb.iter and np.array_equal(ra.x, rb.x)
+
+
+def test_batch_larger_mpc_mix():
+    """A few hundred ragged MPC problems (the batched workload's generator)."""
+    qps = pb.mpc_batch(300, seed=3300)
+    with BatchSolver(qps, precision=B.FP32_MIXED) as bs:
+        bs.solve()
+        res = [bs.result(i) for i in range(len(qps))]
+    bad = [i for i, r in enumerate(res) if r.status != B.SOLVED]
+    assert not bad, bad[:10]
+    for i in range(0, len(qps), 37):
+        prim, dual, ep, ed = acceptance(qps[i], res[i].x, res[i].y, 1e-3, 1e-3)
+        assert prim <= ep * 1.01 and dual <= ed * 1.01
