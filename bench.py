@@ -192,9 +192,10 @@ def batch_main(args, ws, rank, local):
     from paper_1711_08013_gb300 import _binding as B
     from paper_1711_08013_gb300.solver import BatchSolver
 
+    from paper_1711_08013_gb300 import dist as D
     torch.cuda.set_device(local)
     if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        D.init("nccl", torch.device("cuda", local))
     count = int(os.environ.get("OSQP_BATCH_COUNT", "4096"))
     qps = pb.mpc_batch(count, seed=3000 + 100000 * rank)
     prec = B.FP64 if args.precision == "fp64" else B.FP32_MIXED
@@ -229,10 +230,7 @@ def batch_main(args, ws, rank, local):
     iters = sum(r.iter for r in last)
     lat = sorted(r.solve_time for r in last)
     n_solves = count * args.steps
-    if ws > 1:
-        t = torch.tensor([total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t[0])
+    total = D.max_over_ranks(total, device="cuda")
     sv = 8 if prec == B.FP64 else 4
     bytes_launch = sum(admm_bytes(q.n, q.m, q.P_full().nnz + q.A.nnz, q.A.nnz, sv, r.iter,
                                   r.pcg_iters, (r.iter + 24) // 25) for q, r in zip(qps, last))
@@ -334,9 +332,10 @@ def main():
 
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
+    from paper_1711_08013_gb300 import dist as D
     torch.cuda.set_device(local)
     if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        D.init("nccl", torch.device("cuda", local))
 
     cfg, desc, qp = build_problem(args, rank)
     prec = B.FP64 if args.precision == "fp64" else B.FP32_MIXED
@@ -393,14 +392,8 @@ def main():
     pcg = sum(r.pcg_iters for r in infos)
     if any(r.status != B.SOLVED for r in infos):
         raise SystemExit("a timed solve did not converge")
-    if ws > 1:
-        t = torch.tensor([total, float(iters)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_max, iters_all = float(tmax[0]), float(t[1])
-    else:
-        total_max, iters_all = total, float(iters)
+    total_max = D.max_over_ranks(total, device=dev)
+    iters_all = D.sum_over_ranks(float(iters), device=dev)
 
     # end to end through the public C ABI with host buffers: pinned host →
     # device copies of every input, the solve, and a device → host read of
@@ -424,11 +417,7 @@ def main():
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_dt = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_dt], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_dt = float(t[0])
+    e2e_dt = D.max_over_ranks(time.perf_counter() - t0, device=dev)
 
     nnz_kn = qp.P_full().nnz + qp.A.nnz
     sv = 8 if prec == B.FP64 else 4

@@ -16,19 +16,20 @@
 namespace osqpgb {
 namespace host {
 
-
+// Row schedule from row-length statistics.  Rows longer than
+// max(256, 8·mean) are split into kChunk-nonzero chunks handled by whole
+// warps.  The sub-warp width G for the other rows is the largest power of two
+// that still gives every group about one row (32·warps/rows), kept between
+// the width that caps a lane at 16 nonzeros of a mean row and the smallest
+// power of two ≥ the mean row length.  (A wider G would coalesce more of the
+// gathers, but on GB300 the serial chain of dependent loads per group costs
+// more: measured on the Lasso, portfolio, random-QP and MPC workloads.)
 struct SchedHost {
   int group = 1, long_thresh = 256;
   std::vector<int4> chunks;
   std::vector<int> long_rows;
 };
 
-// Row schedule from row-length statistics.  Rows longer than
-// max(256, 8·mean) are split into kChunk-nonzero chunks handled by whole
-// warps.  The sub-warp width G for the other rows is the largest power of two
-// that still gives every group about one row (32·warps/rows), kept between
-// the width that caps a lane at 16 nonzeros of a mean row and the smallest
-// power of two ≥ the mean row length.
 inline int sched_group(double mean_short, long long nshort, long long nwarps) {
   int g_mean = 1;
   while (g_mean < 32 && (double)g_mean < mean_short) g_mean <<= 1;

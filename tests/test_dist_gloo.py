@@ -1,0 +1,70 @@
+"""Multi-rank host logic with two gloo ranks on CPU: problems are sharded by
+work across ranks, each rank solves its share (here with the CPU oracle, so
+no GPU is needed), and the gathered results equal a single-process solve;
+timings combine as max over ranks, counts as sums."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+from paper_1711_08013_gb300 import dist as D
+from paper_1711_08013_gb300 import problems as pb
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_lpt_partition_properties():
+    rng = np.random.default_rng(0)
+    w = rng.lognormal(0, 1.5, size=200)
+    for parts in (1, 2, 3, 8):
+        bins = D.lpt_partition(w, parts)
+        flat = sorted(i for b in bins for i in b)
+        assert flat == list(range(len(w)))
+        loads = [w[b].sum() for b in bins]
+        # LPT guarantee: the heaviest bin is within 4/3 of the optimum (≥ mean, ≥ max item)
+        lower = max(w.sum() / parts, w.max())
+        assert max(loads) <= 4.0 / 3.0 * lower + 1e-9
+    assert D.lpt_partition([5.0, 1.0, 1.0], 2) == [[0], [1, 2]]
+
+
+def _worker(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    from oracle import oracle as O
+    D.init("gloo")
+    qps = pb.mpc_batch(10, seed=3400, nx_range=(3, 6), T_range=(4, 8))
+    weights = [q.A.nnz + q.n + q.m for q in qps]
+    mine = D.shard(weights, rank, world)
+    results = {i: O.solve(qps[i]).x.tolist() for i in mine}
+    gathered = D.gather_objects(results)
+    t = D.max_over_ranks(float(rank + 1))
+    c = D.sum_over_ranks(float(len(mine)))
+    if rank == 0:
+        merged = {}
+        for part in gathered:
+            merged.update(part)
+        np.save(os.path.join(out_dir, "merged.npy"),
+                np.array([merged[i] for i in range(len(qps))], dtype=object), allow_pickle=True)
+        with open(os.path.join(out_dir, "reduced.txt"), "w") as f:
+            f.write(f"{t} {c}\n")
+    import torch.distributed as dist
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_sharded_solve(tmp_path, oracle_mod):
+    port = _free_port()
+    mp.spawn(_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    merged = np.load(tmp_path / "merged.npy", allow_pickle=True)
+    qps = pb.mpc_batch(10, seed=3400, nx_range=(3, 6), T_range=(4, 8))
+    for i, qp in enumerate(qps):
+        ref = oracle_mod.solve(qp).x
+        assert np.array_equal(np.asarray(merged[i]), ref)
+    t, c = map(float, open(tmp_path / "reduced.txt").read().split())
+    assert t == 2.0 and c == 10.0
