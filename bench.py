@@ -40,6 +40,8 @@ WORKLOADS = {
                      "variables (x,y) n=10100, rows m=10101"),
     "mpc_batch": (3, "4096 ragged MPC QPs, nx~U{4..32}, nu=nx/2, T~U{10..30}, one persistent "
                      "launch (cold: scaling + ADMM per problem)"),
+    "serve": (4, "serving: Poisson arrivals at 2000 req/s over a pool of 256 random-QP (m=10n) and "
+                 "256 Huber (100n x n) problem IDs, n~logU[10,NMAX], warm-started perturbed q/l/u"),
 }
 
 
@@ -52,6 +54,9 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lasso")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
+    ap.add_argument("--nmax", type=int, default=500, help="serve: largest problem dimension n")
     return ap.parse_args()
 
 
@@ -317,6 +322,62 @@ def batch_cpu_baseline(qps, sample=256):
                       f"{cores} cores, {dt:.1f} s"}
 
 
+def serve_pool(nmax, seed=4000):
+    spec = pb.serving_pool_spec(seed=seed, pool=256, n_range=(10, nmax))
+    return [pb.random_qp(n, seed=sd) if cls == "random_qp" else pb.huber(n, seed=sd)
+            for cls, n, sd in spec]
+
+
+def serve_main(args, ws, rank, local):
+    """Serving workload: the request stream is the step; value = achieved
+    solves/s, with offered load, p50/p99 latency (arrival → result on the host)
+    and queueing reported beside it."""
+    import torch
+    from paper_1711_08013_gb300 import _binding as B
+    from paper_1711_08013_gb300 import dist as D
+    from paper_1711_08013_gb300.serve import Server, poisson_requests
+    torch.cuda.set_device(local)
+    if ws > 1:
+        D.init("nccl", torch.device("cuda", local))
+    qps = serve_pool(args.nmax, seed=4000 + 7919 * rank)
+    prec = B.FP64 if args.precision == "fp64" else B.FP32_MIXED
+    srv = Server(qps, slots=32, precision=prec)
+    warm = poisson_requests(qps, args.rate, min(2.0, args.duration), seed=1 + rank)
+    srv.run(warm, max_batch=8, deadline=min(2.0, args.duration))
+    reqs = poisson_requests(qps, args.rate, args.duration, seed=100 + rank)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    st = srv.run(reqs, max_batch=8, deadline=args.duration)
+    clocks = sampler.stop()
+    served = [r for r in reqs if r.t_done == r.t_done]
+    bad = sum(r.status != B.SOLVED for r in served)
+    wall = D.max_over_ranks(st.wall, device="cuda")
+    total = D.sum_over_ranks(float(st.requests), device="cuda")
+    line = {
+        "metric": METRIC, "value": total / wall, "unit": UNIT, "n_gpus": ws, "steps": 1,
+        "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == B.FP64 else "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["serve"][1].replace("NMAX", str(args.nmax)),
+                   "offered_req_per_s": args.rate, "duration_s": args.duration,
+                   "pool": len(qps), "slots": 32, "max_batch": 8, "precision": args.precision,
+                   "eps": 1e-3},
+        "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_queue_ms": st.mean_queue_ms,
+        "launches": st.launches, "not_solved": bad, "offered": len(reqs), "dropped": st.dropped,
+        "mean_iters": float(np.mean([r.iter for r in served])) if served else 0.0,
+        "e2e": {"value": total / wall, "unit": UNIT,
+                "h2d_bytes_per_step": int(8 * sum(qps[r.pid].n + 2 * qps[r.pid].m for r in served)),
+                "d2h_bytes_per_step": int(8 * sum(qps[r.pid].n + 2 * qps[r.pid].m for r in served))},
+        "gpu_launches": st.launches, "clocks": clocks,
+    }
+    srv.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -324,6 +385,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.workload == "mpc_batch":
         return batch_main(args, ws, rank, local)
+    if args.workload == "serve":
+        return serve_main(args, ws, rank, local)
 
     import torch
     import torch.distributed as dist

@@ -226,6 +226,32 @@ int32_t osqp_batch_update_vectors(osqp_batch* b, int32_t i, const double* q, con
 int32_t osqp_batch_get(osqp_batch* b, int32_t i, double* x, double* y, double* z,
                        osqp_info* info);
 
+/* ---- overlapping launches (continuous batching) ----------------------------
+ * Up to OSQP_BATCH_MAX_SLOTS subset launches may be in flight at once, each
+ * on its own stream, so problems submitted while others run start as soon
+ * as CTAs free up and their work overlaps on the device.  A problem may be
+ * in at most one launch at a time. */
+#define OSQP_BATCH_MAX_SLOTS 32
+
+/* Copy new q/l/u for the k problems idx[0..k) (host arrays, any pointer
+ * array or entry may be NULL = unchanged; page-locked memory keeps the
+ * copies asynchronous) and launch their warm-started solve on `slot`.
+ * Returns at once; OSQP_ERR_ARG if the slot is busy or a problem is in
+ * flight. */
+int32_t osqp_batch_launch(osqp_batch* b, int32_t slot, const int32_t* idx, int32_t k,
+                          const double* const* q, const double* const* l,
+                          const double* const* u);
+
+/* 1 if the slot is idle or its launch finished (the slot is then retired
+ * and its problems may be read or launched again), 0 if still running. */
+int32_t osqp_batch_slot_query(osqp_batch* b, int32_t slot);
+
+/* Wait for the slot's launch and retire it. */
+int32_t osqp_batch_slot_wait(osqp_batch* b, int32_t slot);
+
+/* Device bytes that problem i occupies (its data, iterates and work arrays). */
+int64_t osqp_batch_footprint(const osqp_batch* b, int32_t i);
+
 int32_t osqp_batch_cleanup(osqp_batch* b);
 
 #ifdef __cplusplus

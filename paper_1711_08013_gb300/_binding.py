@@ -84,7 +84,12 @@ _SIGS = {
     "osqp_batch_update_vectors": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
     "osqp_batch_get": (C.c_int32, [_P, C.c_int32, _P, _P, _P, C.POINTER(osqp_info)]),
     "osqp_batch_cleanup": (C.c_int32, [_P]),
+    "osqp_batch_launch": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, _P, _P, _P]),
+    "osqp_batch_slot_query": (C.c_int32, [_P, C.c_int32]),
+    "osqp_batch_slot_wait": (C.c_int32, [_P, C.c_int32]),
+    "osqp_batch_footprint": (C.c_int64, [_P, C.c_int32]),
 }
+OSQP_BATCH_MAX_SLOTS = 32
 
 
 def lib_path() -> str:
@@ -280,3 +285,46 @@ def osqp_batch_get(h, i, n, m):
 def osqp_batch_cleanup(h):
     if h:
         _check(lib().osqp_batch_cleanup(h), "osqp_batch_cleanup")
+
+
+def osqp_batch_launch(h, slot, idx, q=None, l=None, u=None):
+    """idx: problem indices; q/l/u: None or one host array (or None) per problem."""
+    a = np.ascontiguousarray(idx, np.int32)
+    keep = [a]
+
+    def ptrs(vs):
+        if vs is None:
+            return None
+        arr = (C.c_void_p * len(vs))()
+        for j, v in enumerate(vs):
+            if v is None:
+                arr[j] = None
+            elif isinstance(v, int):
+                arr[j] = v
+            else:
+                vv = np.ascontiguousarray(v, np.float64)
+                keep.append(vv)
+                arr[j] = _ptr(vv)
+        keep.append(arr)
+        return C.cast(arr, C.c_void_p)
+
+    rc = lib().osqp_batch_launch(h, int(slot), _ptr(a), int(a.size), ptrs(q), ptrs(l), ptrs(u))
+    _check(rc, "osqp_batch_launch")
+
+
+def osqp_batch_slot_query(h, slot) -> bool:
+    rc = lib().osqp_batch_slot_query(h, int(slot))
+    if rc < 0:
+        _check(rc, "osqp_batch_slot_query")
+    return rc == 1
+
+
+def osqp_batch_slot_wait(h, slot):
+    _check(lib().osqp_batch_slot_wait(h, int(slot)), "osqp_batch_slot_wait")
+
+
+def osqp_batch_footprint(h, i) -> int:
+    v = lib().osqp_batch_footprint(h, int(i))
+    if v < 0:
+        _check(int(v), "osqp_batch_footprint")
+    return int(v)

@@ -30,11 +30,15 @@ constexpr long long kBatchWarps = kBatchThreads / 32;
 
 enum : int { kModeScale = 1, kModeRefresh = 2, kModeReset = 4 };
 
+// order[k] = problem index | (mode << kModeShift): the mode bits of a
+// problem travel with the launch that solves it, so concurrent launches on
+// different streams never share mutable per-problem flags.
+constexpr int kModeShift = 28;
+
 template <typename T>
 __global__ void __launch_bounds__(kBatchThreads, 2)
     k_batch(const Dev<T>* __restrict__ devs, const int* __restrict__ order, int count,
-            const __grid_constant__ Params P, const int* __restrict__ mode, int* queue,
-            unsigned long long* times) {
+            const __grid_constant__ Params P, int* queue, unsigned long long* times) {
   __shared__ double sm[kSmemDoubles];
   __shared__ int sidx;
   BlockTeam tm{sm};
@@ -44,10 +48,11 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
     const int idx = sidx;
     __syncthreads();
     if (idx >= count) break;
-    const int p = order[idx];
+    const int code = order[idx];
+    const int p = code & ((1 << kModeShift) - 1);
+    const int md = code >> kModeShift;
     const Dev<T>& d = devs[p];
     const unsigned long long t0 = gtimer();
-    const int md = mode[p];
     const double rho_bar = d.sc->rho_bar;
     if (md & kModeScale) {
       scale_stage(tm, d, P, rho_bar, true);
@@ -165,20 +170,27 @@ struct osqp_batch {
   std::vector<ProblemLayout> L;
   std::vector<int> order;           // problems sorted by work, largest first
   std::vector<int> mode;            // per-problem kernel mode for the next launch
-  std::vector<Scalars> sc_host;     // scalars after the last solve
   std::vector<unsigned long long> times_host;
   char* arena = nullptr;
   size_t static_bytes = 0, arena_bytes = 0;
   void* devs = nullptr;             // Dev<T>[count]
   std::vector<char> devs_host;      // host copy of the Dev<T> array
   int* order_d = nullptr;
-  int* mode_d = nullptr;
   int* queue = nullptr;
+  // launch slots for overlapping subset solves (serving)
+  struct Slot {
+    cudaStream_t stream = nullptr;
+    int* order = nullptr;
+    int* queue = nullptr;
+    cudaEvent_t done = nullptr;
+    std::vector<int> members;
+  } slots[OSQP_BATCH_MAX_SLOTS];
+  std::vector<int> inflight;        // slot holding problem i, or -1
+  std::vector<size_t> footprint;    // device bytes of problem i
   unsigned long long* times_d = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   double last_time = 0.0;
   bool solved = false;
-  bool dirty = false;  // a launch has not been collected into sc_host yet
 };
 
 namespace {
@@ -219,46 +231,47 @@ void fill_batch_devs(osqp_batch* b) {
 }
 
 template <typename T>
-int launch_batch(osqp_batch* b, const int* order_d, int count) {
-  if (cudaMemcpyAsync(b->mode_d, b->mode.data(), sizeof(int) * b->count, cudaMemcpyHostToDevice,
-                      b->stream) != cudaSuccess)
+int launch_batch(osqp_batch* b, const std::vector<int>& sel, int* order_d, int* queue,
+                 cudaStream_t st) {
+  const int count = (int)sel.size();
+  std::vector<int> code(count);
+  for (int k = 0; k < count; ++k) code[k] = sel[k] | (b->mode[sel[k]] << kModeShift);
+  if (cudaMemcpyAsync(order_d, code.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
     return OSQP_ERR_CUDA;
-  if (cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
+  // the host vector must outlive the copy: wait for it (small, pageable)
+  if (cudaStreamSynchronize(st) != cudaSuccess) return OSQP_ERR_CUDA;
+  if (cudaMemsetAsync(queue, 0, sizeof(int), st) != cudaSuccess) return OSQP_ERR_CUDA;
   const int grid = std::max(1, std::min(b->grid, count));
-  k_batch<T><<<grid, kBatchThreads, 0, b->stream>>>((const Dev<T>*)b->devs, order_d, count, b->P,
-                                                     b->mode_d, b->queue, b->times_d);
-  return cudaGetLastError() == cudaSuccess ? OSQP_OK : OSQP_ERR_CUDA;
-}
-
-int batch_launch(osqp_batch* b, const int* order_d, int count) {
-  if (cudaEventRecord(b->ev[0], b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
-  const int rc = b->set.precision == OSQP_PRECISION_FP64 ? launch_batch<double>(b, order_d, count)
-                                                         : launch_batch<float>(b, order_d, count);
-  if (rc) return rc;
-  if (cudaEventRecord(b->ev[1], b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
-  b->solved = true;
-  b->dirty = true;
+  k_batch<T><<<grid, kBatchThreads, 0, st>>>((const Dev<T>*)b->devs, order_d, count, b->P, queue,
+                                              b->times_d);
+  if (cudaGetLastError() != cudaSuccess) return OSQP_ERR_CUDA;
+  for (int v : sel) b->mode[v] = 0;
   return OSQP_OK;
 }
 
-int batch_collect(osqp_batch* b) {
-  // Scalars of every problem (they sit at the same offset in each dynamic block).
-  for (int i = 0; i < b->count; ++i) {
-    const Scalars* src = b->set.precision == OSQP_PRECISION_FP64 ? dev_at<double>(b, i)->sc
-                                                                 : dev_at<float>(b, i)->sc;
-    if (cudaMemcpyAsync(&b->sc_host[i], src, sizeof(Scalars), cudaMemcpyDeviceToHost, b->stream) !=
-        cudaSuccess)
-      return OSQP_ERR_CUDA;
-  }
-  if (cudaMemcpyAsync(b->times_host.data(), b->times_d, sizeof(unsigned long long) * 2 * b->count,
-                      cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
-    return OSQP_ERR_CUDA;
+int batch_launch(osqp_batch* b, const std::vector<int>& sel) {
+  if (cudaEventRecord(b->ev[0], b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
+  const int rc = b->set.precision == OSQP_PRECISION_FP64
+                     ? launch_batch<double>(b, sel, b->order_d, b->queue, b->stream)
+                     : launch_batch<float>(b, sel, b->order_d, b->queue, b->stream);
+  if (rc) return rc;
+  if (cudaEventRecord(b->ev[1], b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
+  b->solved = true;
+  return OSQP_OK;
+}
+
+int batch_wait(osqp_batch* b) {
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
   float ms = 0.f;
   if (b->solved && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess)
     b->last_time = ms * 1e-3;
-  b->dirty = false;
   return OSQP_OK;
+}
+
+template <typename T>
+const Scalars* scalars_of(osqp_batch* b, int i) {
+  return dev_at<T>(b, i)->sc;
 }
 
 }  // namespace
@@ -343,7 +356,6 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
   }
   if (cudaMalloc(&b->devs, dev_bytes) != cudaSuccess ||
       cudaMalloc((void**)&b->order_d, sizeof(int) * count) != cudaSuccess ||
-      cudaMalloc((void**)&b->mode_d, sizeof(int) * count) != cudaSuccess ||
       cudaMalloc((void**)&b->queue, sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&b->times_d, sizeof(unsigned long long) * 2 * count) != cudaSuccess) {
     cudaGetLastError();
@@ -404,13 +416,23 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
   if (cudaMemcpy(b->devs, b->devs_host.data(), dev_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(OSQP_ERR_CUDA);
   // Scalars: ρ̄⁰ for every problem; the first launch scales every problem.
-  b->sc_host.assign(count, Scalars{});
-  for (int i = 0; i < count; ++i) b->sc_host[i].rho_bar = settings->rho;
+  {
+    Scalars init{};
+    init.rho_bar = settings->rho;
+    for (int i = 0; i < count; ++i) {
+      Scalars* dst = settings->precision == OSQP_PRECISION_FP64 ? dev_at<double>(b, i)->sc
+                                                               : dev_at<float>(b, i)->sc;
+      if (cudaMemcpy(dst, &init, sizeof(Scalars), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(OSQP_ERR_CUDA);
+    }
+  }
+  b->inflight.assign(count, -1);
+  b->footprint.resize(count);
   for (int i = 0; i < count; ++i) {
-    Scalars* dst = settings->precision == OSQP_PRECISION_FP64 ? dev_at<double>(b, i)->sc
-                                                             : dev_at<float>(b, i)->sc;
-    if (cudaMemcpy(dst, &b->sc_host[i], sizeof(Scalars), cudaMemcpyHostToDevice) != cudaSuccess)
-      return fail(OSQP_ERR_CUDA);
+    const size_t dyn = settings->precision == OSQP_PRECISION_FP64
+                           ? dynamic_carve<double>(b->L[i], nullptr, nullptr)
+                           : dynamic_carve<float>(b->L[i], nullptr, nullptr);
+    b->footprint[i] = static_offsets(b->L[i]).end + dyn;
   }
   b->mode.assign(count, kModeScale);
   b->times_host.assign(2 * (size_t)count, 0);
@@ -430,18 +452,17 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
 
 int32_t osqp_batch_solve_async(osqp_batch* b) {
   if (!b) return OSQP_ERR_ARG;
+  for (int v : b->inflight)
+    if (v >= 0) return OSQP_ERR_ARG;  // a slot launch is still in flight
   if (!b->set.warm_start)
     for (int i = 0; i < b->count; ++i) b->mode[i] |= kModeReset;
-  const int rc = batch_launch(b, b->order_d, b->count);
-  if (rc) return rc;
-  std::fill(b->mode.begin(), b->mode.end(), 0);
-  return OSQP_OK;
+  return batch_launch(b, b->order);
 }
 
 int32_t osqp_batch_solve(osqp_batch* b) {
   const int rc = osqp_batch_solve_async(b);
   if (rc) return rc;
-  return batch_collect(b);
+  return batch_wait(b);
 }
 
 int32_t osqp_batch_solve_subset(osqp_batch* b, const int32_t* idx, int32_t k) {
@@ -449,30 +470,20 @@ int32_t osqp_batch_solve_subset(osqp_batch* b, const int32_t* idx, int32_t k) {
   if (k == 0) return OSQP_OK;
   std::vector<int> sel(idx, idx + k);
   for (int v : sel)
-    if (v < 0 || v >= b->count) return OSQP_ERR_ARG;
+    if (v < 0 || v >= b->count || b->inflight[v] >= 0) return OSQP_ERR_ARG;
   std::stable_sort(sel.begin(), sel.end(), [&](int a, int c) {
     return (long long)b->L[a].nnz_kn + b->L[a].nnz_a > (long long)b->L[c].nnz_kn + b->L[c].nnz_a;
   });
   if (!b->set.warm_start)
     for (int v : sel) b->mode[v] |= kModeReset;
-  // the subset takes the front of the order buffer for this launch
-  if (cudaMemcpyAsync(b->order_d, sel.data(), sizeof(int) * k, cudaMemcpyHostToDevice, b->stream) !=
-      cudaSuccess)
-    return OSQP_ERR_CUDA;
-  int rc = batch_launch(b, b->order_d, k);
+  const int rc = batch_launch(b, sel);
   if (rc) return rc;
-  for (int v : sel) b->mode[v] = 0;
-  // restore the full order for the next whole-batch launch
-  if (cudaMemcpyAsync(b->order_d, b->order.data(), sizeof(int) * b->count, cudaMemcpyHostToDevice,
-                      b->stream) != cudaSuccess)
-    return OSQP_ERR_CUDA;
-  return batch_collect(b);
+  return batch_wait(b);
 }
 
 int32_t osqp_batch_reset(osqp_batch* b) {
   if (!b) return OSQP_ERR_ARG;
   std::fill(b->mode.begin(), b->mode.end(), (int)kModeScale);
-  for (int i = 0; i < b->count; ++i) b->sc_host[i].rho_bar = b->set.rho;
   for (int i = 0; i < b->count; ++i) {
     Scalars* dst = b->set.precision == OSQP_PRECISION_FP64 ? dev_at<double>(b, i)->sc
                                                           : dev_at<float>(b, i)->sc;
@@ -483,22 +494,18 @@ int32_t osqp_batch_reset(osqp_batch* b) {
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? OSQP_OK : OSQP_ERR_CUDA;
 }
 
-int32_t osqp_batch_update_vectors(osqp_batch* b, int32_t i, const double* q, const double* l,
-                                  const double* u) {
-  if (!b || i < 0 || i >= b->count) return OSQP_ERR_ARG;
+static int32_t copy_vectors(osqp_batch* b, int i, const double* q, const double* l,
+                            const double* u, cudaStream_t st) {
   const ProblemLayout& L = b->L[i];
   if (q && !finite_all(q, L.n)) return OSQP_ERR_NONFINITE;
   const StaticOffsets o = static_offsets(L);
   char* sb = b->arena + L.s_off;
   if (l || u) {
     std::vector<double> lh(L.m), uh(L.m);
-    if (!l && L.m &&
-        cudaMemcpyAsync(lh.data(), sb + o.l, sizeof(double) * L.m, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    if (!l && L.m && cudaMemcpy(lh.data(), sb + o.l, sizeof(double) * L.m, cudaMemcpyDeviceToHost) != cudaSuccess)
       return OSQP_ERR_CUDA;
-    if (!u && L.m &&
-        cudaMemcpyAsync(uh.data(), sb + o.u, sizeof(double) * L.m, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    if (!u && L.m && cudaMemcpy(uh.data(), sb + o.u, sizeof(double) * L.m, cudaMemcpyDeviceToHost) != cudaSuccess)
       return OSQP_ERR_CUDA;
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
     const double* Lv = l ? l : lh.data();
     const double* Uv = u ? u : uh.data();
     for (int r = 0; r < L.m; ++r) {
@@ -506,37 +513,120 @@ int32_t osqp_batch_update_vectors(osqp_batch* b, int32_t i, const double* q, con
       if (Lv[r] > Uv[r]) return OSQP_ERR_LGTU;
     }
   }
-  if (q && cudaMemcpyAsync(sb + o.q, q, sizeof(double) * L.n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+  if (q && cudaMemcpyAsync(sb + o.q, q, sizeof(double) * L.n, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return OSQP_ERR_CUDA;
-  if (l && L.m && cudaMemcpyAsync(sb + o.l, l, sizeof(double) * L.m, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+  if (l && L.m && cudaMemcpyAsync(sb + o.l, l, sizeof(double) * L.m, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return OSQP_ERR_CUDA;
-  if (u && L.m && cudaMemcpyAsync(sb + o.u, u, sizeof(double) * L.m, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+  if (u && L.m && cudaMemcpyAsync(sb + o.u, u, sizeof(double) * L.m, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return OSQP_ERR_CUDA;
-  if (!(b->mode[i] & kModeScale)) b->mode[i] |= kModeRefresh;
+  if (q || l || u)
+    if (!(b->mode[i] & kModeScale)) b->mode[i] |= kModeRefresh;
   return OSQP_OK;
+}
+
+int32_t osqp_batch_update_vectors(osqp_batch* b, int32_t i, const double* q, const double* l,
+                                  const double* u) {
+  if (!b || i < 0 || i >= b->count || b->inflight[i] >= 0) return OSQP_ERR_ARG;
+  const int rc = copy_vectors(b, i, q, l, u, b->stream);
+  if (rc) return rc;
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? OSQP_OK : OSQP_ERR_CUDA;
+}
+
+int32_t osqp_batch_launch(osqp_batch* b, int32_t slot, const int32_t* idx, int32_t k,
+                          const double* const* q, const double* const* l, const double* const* u) {
+  if (!b || slot < 0 || slot >= OSQP_BATCH_MAX_SLOTS || k < 1 || k > b->count || !idx)
+    return OSQP_ERR_ARG;
+  osqp_batch::Slot& S = b->slots[slot];
+  if (!S.members.empty()) return OSQP_ERR_ARG;  // previous launch not retired
+  std::vector<int> sel(idx, idx + k);
+  for (int v : sel)
+    if (v < 0 || v >= b->count || b->inflight[v] >= 0) return OSQP_ERR_ARG;
+  if (!S.stream) {
+    if (cudaStreamCreateWithFlags(&S.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc((void**)&S.order, sizeof(int) * b->count) != cudaSuccess ||
+        cudaMalloc((void**)&S.queue, sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return OSQP_ERR_CUDA;
+    }
+  }
+  for (int j = 0; j < k; ++j) {
+    const int rc = copy_vectors(b, sel[j], q ? q[j] : nullptr, l ? l[j] : nullptr,
+                                u ? u[j] : nullptr, S.stream);
+    if (rc) return rc;
+  }
+  if (!b->set.warm_start)
+    for (int v : sel) b->mode[v] |= kModeReset;
+  std::stable_sort(sel.begin(), sel.end(), [&](int a, int c) {
+    return (long long)b->L[a].nnz_kn + b->L[a].nnz_a > (long long)b->L[c].nnz_kn + b->L[c].nnz_a;
+  });
+  const int rc = b->set.precision == OSQP_PRECISION_FP64
+                     ? launch_batch<double>(b, sel, S.order, S.queue, S.stream)
+                     : launch_batch<float>(b, sel, S.order, S.queue, S.stream);
+  if (rc) return rc;
+  if (cudaEventRecord(S.done, S.stream) != cudaSuccess) return OSQP_ERR_CUDA;
+  for (int v : sel) b->inflight[v] = slot;
+  S.members = sel;
+  return OSQP_OK;
+}
+
+static void retire(osqp_batch* b, int slot) {
+  osqp_batch::Slot& S = b->slots[slot];
+  for (int v : S.members) b->inflight[v] = -1;
+  S.members.clear();
+}
+
+int32_t osqp_batch_slot_query(osqp_batch* b, int32_t slot) {
+  if (!b || slot < 0 || slot >= OSQP_BATCH_MAX_SLOTS) return OSQP_ERR_ARG;
+  osqp_batch::Slot& S = b->slots[slot];
+  if (S.members.empty()) return 1;
+  const cudaError_t e = cudaEventQuery(S.done);
+  if (e == cudaErrorNotReady) return 0;
+  if (e != cudaSuccess) return OSQP_ERR_CUDA;
+  retire(b, slot);
+  return 1;
+}
+
+int32_t osqp_batch_slot_wait(osqp_batch* b, int32_t slot) {
+  if (!b || slot < 0 || slot >= OSQP_BATCH_MAX_SLOTS) return OSQP_ERR_ARG;
+  osqp_batch::Slot& S = b->slots[slot];
+  if (S.members.empty()) return OSQP_OK;
+  if (cudaEventSynchronize(S.done) != cudaSuccess) return OSQP_ERR_CUDA;
+  retire(b, slot);
+  return OSQP_OK;
+}
+
+int64_t osqp_batch_footprint(const osqp_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= b->count) return OSQP_ERR_ARG;
+  return (int64_t)b->footprint[i];
 }
 
 int32_t osqp_batch_get(osqp_batch* b, int32_t i, double* x, double* y, double* z,
                        osqp_info* info) {
   if (!b || i < 0 || i >= b->count) return OSQP_ERR_ARG;
+  if (b->inflight[i] >= 0) {
+    const int rc = osqp_batch_slot_wait(b, b->inflight[i]);
+    if (rc) return rc;
+  }
   const ProblemLayout& L = b->L[i];
   const bool f64 = b->set.precision == OSQP_PRECISION_FP64;
   const double* xo = f64 ? dev_at<double>(b, i)->x_out : dev_at<float>(b, i)->x_out;
   const double* yo = f64 ? dev_at<double>(b, i)->y_out : dev_at<float>(b, i)->y_out;
   const double* zo = f64 ? dev_at<double>(b, i)->z_out : dev_at<float>(b, i)->z_out;
-  if (z && L.m && cudaMemcpyAsync(z, zo, sizeof(double) * L.m, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
-    return OSQP_ERR_CUDA;
-  if (x && cudaMemcpyAsync(x, xo, sizeof(double) * L.n, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
-    return OSQP_ERR_CUDA;
-  if (y && L.m && cudaMemcpyAsync(y, yo, sizeof(double) * L.m, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
-    return OSQP_ERR_CUDA;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
+  if (x && cudaMemcpy(x, xo, sizeof(double) * L.n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (y && L.m && cudaMemcpy(y, yo, sizeof(double) * L.m, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (z && L.m && cudaMemcpy(z, zo, sizeof(double) * L.m, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OSQP_ERR_CUDA;
   if (info) {
-    if (b->dirty) {
-      const int rc = batch_collect(b);
-      if (rc) return rc;
-    }
-    const Scalars& s = b->sc_host[i];
+    Scalars s;
+    unsigned long long t[2];
+    const Scalars* src = f64 ? scalars_of<double>(b, i) : scalars_of<float>(b, i);
+    if (cudaMemcpy(&s, src, sizeof(Scalars), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(t, b->times_d + 2 * (size_t)i, sizeof(t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return OSQP_ERR_CUDA;
     std::memset(info, 0, sizeof(*info));
     info->status = s.status;
     info->iter = s.iter;
@@ -548,9 +638,8 @@ int32_t osqp_batch_get(osqp_batch* b, int32_t i, double* x, double* y, double* z
     info->prim_res = s.prim_res;
     info->dual_res = s.dual_res;
     info->rho_estimate = s.rho_bar;
-    const unsigned long long t0 = b->times_host[2 * (size_t)i], t1 = b->times_host[2 * (size_t)i + 1];
-    info->solve_time = t1 > t0 ? (double)(t1 - t0) * 1e-9 : 0.0;
-    info->setup_time = b->last_time;  // whole-launch device time
+    info->solve_time = t[1] > t[0] ? (double)(t[1] - t[0]) * 1e-9 : 0.0;
+    info->setup_time = b->last_time;  // device time of the last whole-batch launch
   }
   return OSQP_OK;
 }
@@ -559,7 +648,16 @@ int32_t osqp_batch_cleanup(osqp_batch* b) {
   if (!b) return OSQP_ERR_ARG;
   int rc = OSQP_OK;
   if (b->arena && cudaStreamSynchronize(b->stream) != cudaSuccess) rc = OSQP_ERR_CUDA;
-  void* ptrs[] = {b->arena, b->devs, b->order_d, b->mode_d, b->queue, b->times_d};
+  for (auto& S : b->slots) {
+    if (S.stream) {
+      if (cudaStreamSynchronize(S.stream) != cudaSuccess) rc = OSQP_ERR_CUDA;
+      cudaStreamDestroy(S.stream);
+    }
+    if (S.order) cudaFree(S.order);
+    if (S.queue) cudaFree(S.queue);
+    if (S.done) cudaEventDestroy(S.done);
+  }
+  void* ptrs[] = {b->arena, b->devs, b->order_d, b->queue, b->times_d};
   for (void* p : ptrs)
     if (p && cudaFree(p) != cudaSuccess) rc = OSQP_ERR_CUDA;
   for (auto& ev : b->ev)

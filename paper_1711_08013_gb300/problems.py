@@ -363,22 +363,14 @@ def config_problem(config: int, instance: int = 0, **kw) -> QP:
 
 
 def perturb_vectors(rng: np.random.Generator, qp: QP, scale: float = 0.05):
-    """Serving-request perturbation of (q, l, u): v + scale·N(0,1)·(1+|v|) on
-    finite entries; an equality row keeps l = u."""
-    def pert(v):
-        out = v.copy()
-        fin = np.isfinite(v)
-        out[fin] = v[fin] + scale * rng.standard_normal(int(fin.sum())) * (1.0 + np.abs(v[fin]))
-        return out
-    q = pert(qp.q)
-    eq = qp.l == qp.u
-    l = pert(qp.l)
-    u = pert(qp.u)
-    u[eq] = l[eq]
-    bad = l > u
-    mid = 0.5 * (l[bad] + u[bad])
-    l[bad] = mid
-    u[bad] = mid
+    """Serving-request perturbation: q_j + scale·N(0,1)·(1+|q_j|); each row's
+    bounds are multiplied by one factor max(0.5, 1 + scale·N(0,1)), which
+    keeps l ≤ u, equality rows equal, infinite bounds infinite and 0 inside
+    [l, u] wherever it was."""
+    q = qp.q + scale * rng.standard_normal(qp.n) * (1.0 + np.abs(qp.q))
+    f = np.maximum(0.5, 1.0 + scale * rng.standard_normal(qp.m))
+    l = np.where(np.isfinite(qp.l), qp.l * f, qp.l)
+    u = np.where(np.isfinite(qp.u), qp.u * f, qp.u)
     return q, l, u
 
 

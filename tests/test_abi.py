@@ -27,7 +27,8 @@ def declared_functions():
     names = []
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
-        names += re.findall(r"^\s*(?:int32_t|void|const char\s*\*)\s+(osqp_\w+)\s*\(", text, re.M)
+        names += re.findall(r"^\s*(?:int32_t|int64_t|void|const char\s*\*)\s+(osqp_\w+)\s*\(", text,
+                            re.M)
     return sorted(set(names))
 
 

@@ -1,0 +1,83 @@
+"""Continuous-batching serving: requests overlap on the device, each result
+equals the result of the same request served alone, results pass the
+acceptance test against the perturbed problems, and the in-flight device
+footprint stays within the admission budget."""
+import numpy as np
+import pytest
+
+from paper_1711_08013_gb300 import _binding as B
+from paper_1711_08013_gb300 import problems as pb
+from tests.kkt_check import acceptance
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1711_08013_gb300.serve import Request, Server, poisson_requests  # noqa: E402
+
+
+def pool():
+    qps = [pb.random_qp(int(n), seed=4100 + k) for k, n in enumerate((10, 16, 24, 40, 60, 90))]
+    qps += [pb.huber(int(n), seed=4200 + k) for k, n in enumerate((3, 4, 6, 8, 10, 12))]
+    return qps
+
+
+def clone(reqs):
+    return [Request(r.pid, r.t_arrival, r.q, r.l, r.u) for r in reqs]
+
+
+def test_serving_overlap_matches_alone_and_oracle(oracle_mod):
+    qps = pool()
+    reqs = poisson_requests(qps, rate=2000.0, duration=0.05, seed=11)
+    assert len(reqs) > 40
+    with Server(qps, slots=4) as srv:
+        mix = clone(reqs)
+        st = srv.run(mix, keep_x=True)
+    with Server(qps, slots=1) as srv1:
+        alone = clone(reqs)
+        st1 = srv1.run(alone, max_batch=1, keep_x=True)
+    assert st.launches < st1.launches  # requests were batched / overlapped
+    assert all(r.status == B.SOLVED for r in mix) and all(r.status == B.SOLVED for r in alone), \
+        sorted({(r.pid, r.status) for r in mix + alone if r.status != B.SOLVED})
+    for a, b in zip(sorted(mix, key=lambda r: r.t_arrival), sorted(alone, key=lambda r: r.t_arrival)):
+        assert a.pid == b.pid
+        # Huber instances have long columns (atomically combined chunks):
+        # rounding-level agreement; the others are bit-identical.
+        if qps[a.pid].meta.get("cls") == "huber":
+            assert np.allclose(a.x, b.x, rtol=1e-7, atol=1e-9)
+        else:
+            assert np.array_equal(a.x, b.x)
+    # the last request of each problem ID: its (x, y) are still resident
+    last = {}
+    for r in sorted(mix, key=lambda r: r.t_arrival):
+        last[r.pid] = r
+    with Server(qps, slots=4) as srv:
+        srv.run(clone(reqs))
+        for pid, r in last.items():
+            x, y, z, info = B.osqp_batch_get(srv.h, pid, qps[pid].n, qps[pid].m)
+            qp2 = pb._finish("req", qps[pid].P, r.q, qps[pid].A, r.l, r.u)
+            prim, dual, ep, ed = acceptance(qp2, x, y, 1e-3, 1e-3)
+            assert prim <= 1.01 * ep and dual <= 1.01 * ed, (pid, prim, ep, dual, ed)
+            o = oracle_mod.solve(qp2)
+            assert o.status == oracle_mod.SOLVED
+
+
+def test_deadline_drops_unlaunched_requests():
+    qps = pool()
+    reqs = poisson_requests(qps, rate=50000.0, duration=0.05, seed=13)
+    with Server(qps, slots=2) as srv:
+        st = srv.run(clone(reqs), deadline=0.0)
+    assert st.requests + st.dropped == len(reqs)
+
+
+def test_footprint_budget_limits_inflight_work():
+    qps = pool()
+    reqs = poisson_requests(qps, rate=5000.0, duration=0.02, seed=12)
+    with Server(qps, slots=4, prime=True) as srv:
+        budget = max(srv.footprint) + min(srv.footprint)
+        srv.budget = budget
+        st = srv.run(clone(reqs))
+    assert st.max_inflight_bytes <= budget
+    assert st.requests == len(reqs)
