@@ -134,7 +134,7 @@ size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
   const size_t kn_v = b.take<T>(L.nnz_kn);
   const size_t a_v = b.take<T>(L.nnz_a);
   const size_t rt = b.take<uint8_t>(m);
-  size_t on[15], om[19], otn[10], otm[3];
+  size_t on[15], om[19], otn[11], otm[6];
   for (auto& v : on) v = b.take<double>(n);
   for (auto& v : om) v = b.take<double>(m);
   for (auto& v : otn) v = b.take<T>(n);
@@ -151,10 +151,11 @@ size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
                      &d->dy, &d->ax, &d->adx, &d->azt, &d->z_out, &d->y_out, &d->pcert,
                      &d->zt, &d->wm, &d->um, &d->Einv};
     for (int k = 0; k < 19; ++k) *mv[k] = (double*)(base + om[k]);
-    T** tn[] = {&d->dinv, &d->b, &d->mr, &d->p, &d->r0, &d->r1, &d->s0, &d->s1, &d->w0, &d->w1};
-    for (int k = 0; k < 10; ++k) *tn[k] = (T*)(base + otn[k]);
-    T** tmv[] = {&d->rt0, &d->rt1, &d->ap};
-    for (int k = 0; k < 3; ++k) *tmv[k] = (T*)(base + otm[k]);
+    T** tn[] = {&d->dinv, &d->b, &d->mr, &d->p, &d->r0, &d->r1, &d->s0, &d->s1, &d->w0, &d->w1,
+                &d->dxt};
+    for (int k = 0; k < 11; ++k) *tn[k] = (T*)(base + otn[k]);
+    T** tmv[] = {&d->rt0, &d->rt1, &d->ap, &d->dzt, &d->rhoT, &d->rho_invT};
+    for (int k = 0; k < 6; ++k) *tmv[k] = (T*)(base + otm[k]);
     d->sc = (Scalars*)(base + sc);
   }
   return (b.off + 255) & ~(size_t)255;

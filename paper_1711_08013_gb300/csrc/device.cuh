@@ -88,6 +88,9 @@ struct Dev {
   // and t = R·Ā·mr double-buffered; ap = Āp (for z̃ = Āx̃)
   T *b, *mr, *p, *r0, *r1, *s0, *s1, *w0, *w1;
   T *rt0, *rt1, *ap;
+  // PCG corrections of x̃ and z̃ in working precision, folded into the FP64
+  // x̃, z̃ once per ADMM iteration; working-precision copies of ρ and ρ⁻¹
+  T *dxt, *dzt, *rhoT, *rho_invT;
   double *px, *aty, *pdx, *atdy, *ax, *adx, *azt;
   double *x_out, *y_out, *z_out, *pcert, *dcert;
   Scalars* sc;
@@ -577,6 +580,8 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
     const double rh = rho_of(t, rho_bar);
     d.rho[i] = rh;
     d.rho_inv[i] = 1.0 / rh;
+    d.rhoT[i] = T(rh);
+    d.rho_invT[i] = T(1.0 / rh);
   }
   if (!tm.sync()) return false;
   jacobi_rows(tm, d, P.sigma, rho_bar);
@@ -625,6 +630,8 @@ __device__ bool refresh_stage(Team& tm, const Dev<T>& d, const Params& P, double
     const double rh = rho_of(t, rho_bar);
     d.rho[i] = rh;
     d.rho_inv[i] = 1.0 / rh;
+    d.rhoT[i] = T(rh);
+    d.rho_invT[i] = T(1.0 / rh);
   }
   if (!tm.sync()) return false;
   jacobi_rows(tm, d, P.sigma, rho_bar);
@@ -668,6 +675,10 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   auto wbuf = [&](int i) { return i ? d.w1 : d.w0; };
   auto tbuf = [&](int i) { return i ? d.rt1 : d.rt0; };
   T* __restrict__ dinv = d.dinv;
+  T* __restrict__ dxt = d.dxt;
+  T* __restrict__ dzt = d.dzt;
+  const T* __restrict__ rhoT = d.rhoT;
+  const T* __restrict__ rho_invT = d.rho_invT;
   const double* __restrict__ rho = d.rho;
   const double* __restrict__ rho_inv = d.rho_inv;
 
@@ -681,7 +692,9 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     const double rh = rho[i];
     wm[i] = rh * z[i] - y[i];
     um[i] = rh * (z[i] - zt[i]) - y[i];
+    dzt[i] = T(0);
   }
+  for (int j = tid; j < n; j += nth) dxt[j] = T(0);
   zero_long(tm, d.kn, rbuf(cur));
   zero_long(tm, d.kn, bv);
   zero_long(tm, d.as, tbuf(cur));
@@ -734,19 +747,23 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     {
       const T* __restrict__ r = rbuf(cur);
       T* __restrict__ t = tbuf(cur);
+      T a0 = T(0), a1 = T(0), a2 = T(0);
       for (int j = tid; j < n; j += nth) {
         const T rj = r[j];
         const T uj = rj * dinv[j];
         u[j] = uj;
-        red3[0] += (double)rj * (double)uj;
-        red3[1] = fmax(red3[1], fabs((double)rj));
-        red3[2] = fmax(red3[2], fabs((double)bv[j]));
+        a0 += rj * uj;
+        a1 = fmax(a1, fabs(rj));
+        a2 = fmax(a2, fabs(bv[j]));
       }
+      red3[0] = (double)a0;
+      red3[1] = (double)a1;
+      red3[2] = (double)a2;
       spmv<1, false, T, T>(
           tm, d.as, a_rp, a_ci, a_v,
           [&](int col, T v, T* acc) { acc[0] += v * (r[col] * dinv[col]); },
-          [&](int i, T* acc) { t[i] = T(rho[i] * (double)acc[0]); },
-          [&](int i, int, T* acc) { atomicAdd(&t[i], T(rho[i] * (double)acc[0])); });
+          [&](int i, T* acc) { t[i] = rhoT[i] * acc[0]; },
+          [&](int i, int, T* acc) { atomicAdd(&t[i], rhoT[i] * acc[0]); });
       zero_long(tm, d.kn, wbuf(cur));
     }
     tm.template publish<3, 6u>(red3);
@@ -762,6 +779,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     if (!done) {
       // --- W: w = Ku, (w,u)
       double red1[1] = {0.0};
+      T wacc = T(0);
       T* __restrict__ w = wbuf(cur);
       const T* __restrict__ tg = tbuf(cur);
       spmv<1, false, T, T>(
@@ -770,13 +788,14 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           [&](int j, T* acc) {
             const T wj = T(sigma) * u[j] + acc[0];
             w[j] = wj;
-            red1[0] += (double)wj * (double)u[j];
+            wacc += wj * u[j];
           },
           [&](int j, int first, T* acc) {
             const T part = acc[0] + (first ? T(sigma) * u[j] : T(0));
             atomicAdd(&w[j], part);
-            red1[0] += (double)part * (double)u[j];
+            wacc += part * u[j];
           });
+      red1[0] = (double)wacc;
       tm.template publish<1, 0u>(red1);
       if (!tm.sync()) return false;
       tm.template collect<1, 0u>(red1);
@@ -802,16 +821,16 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           const T sj = first ? wc[j] : wc[j] + bT * sc[j];
           pv[j] = pj;
           sn[j] = sj;
-          xt[j] += alpha_c * (double)pj;
+          dxt[j] += aT * pj;
           const T rj = rc[j] - aT * sj;
           rn[j] = rj;
           u[j] = rj * dinv[j];
         }
         for (int i = tid; i < m; i += nth) {
-          const T ti = T(rho_inv[i] * (double)tc[i]);
+          const T ti = rho_invT[i] * tc[i];
           const T api = first ? ti : ti + bT * ap[i];
           ap[i] = api;
-          zt[i] += alpha_c * (double)api;
+          dzt[i] += aT * api;
         }
         zero_long(tm, d.kn, wbuf(nxt));
       }
@@ -821,8 +840,8 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         T* __restrict__ tn = tbuf(nxt);
         spmv<1, false, T, T>(
             tm, d.as, a_rp, a_ci, a_v, [&](int col, T v, T* acc) { acc[0] += v * u[col]; },
-            [&](int i, T* acc) { tn[i] = T(rho[i] * (double)acc[0]); },
-            [&](int i, int, T* acc) { atomicAdd(&tn[i], T(rho[i] * (double)acc[0])); });
+            [&](int i, T* acc) { tn[i] = rhoT[i] * acc[0]; },
+            [&](int i, int, T* acc) { atomicAdd(&tn[i], rhoT[i] * acc[0]); });
       }
       if (!tm.sync()) return false;
       ++j_it;
@@ -832,10 +851,11 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       {
         const T* __restrict__ rn = rbuf(nxt);
         T* __restrict__ wn = wbuf(nxt);
+        T g0 = T(0), g1 = T(0), g2 = T(0);
         for (int j = tid; j < n; j += nth) {
           const T rj = rn[j];
-          red2[0] += (double)rj * (double)u[j];
-          red2[2] = fmax(red2[2], fabs((double)rj));
+          g0 += rj * u[j];
+          g2 = fmax(g2, fabs(rj));
         }
         const T* __restrict__ tg = tbuf(nxt);
         spmv<1, false, T, T>(
@@ -844,14 +864,17 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
             [&](int j, T* acc) {
               const T wj = T(sigma) * u[j] + acc[0];
               wn[j] = wj;
-              red2[1] += (double)wj * (double)u[j];
+              g1 += wj * u[j];
             },
             [&](int j, int first2, T* acc) {
               const T part = acc[0] + (first2 ? T(sigma) * u[j] : T(0));
               atomicAdd(&wn[j], part);
-              red2[1] += (double)part * (double)u[j];
+              g1 += part * u[j];
             });
         zero_long(tm, d.as, tbuf(cur));
+        red2[0] = (double)g0;
+        red2[1] = (double)g1;
+        red2[2] = (double)g2;
       }
       tm.template publish<3, 4u>(red2);
       if (!tm.sync()) return false;
@@ -869,13 +892,18 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
 
     // --- U: Algorithm 1 steps 5–7, y in the form ρ(v − Π(v)) of Eq. (zy-update)
     for (int j = tid; j < n; j += nth) {
-      const double xn = alpha * xt[j] + (1.0 - alpha) * x[j];
+      const double xtj = xt[j] + (double)dxt[j];
+      xt[j] = xtj;
+      dxt[j] = T(0);
+      const double xn = alpha * xtj + (1.0 - alpha) * x[j];
       d.dx[j] = xn - x[j];
       x[j] = xn;
     }
     for (int i = tid; i < m; i += nth) {
       const double rh = rho[i];
-      const double zti = zt[i];
+      const double zti = zt[i] + (double)dzt[i];
+      zt[i] = zti;
+      dzt[i] = T(0);
       const double v = alpha * zti + (1.0 - alpha) * z[i] + rho_inv[i] * y[i];
       const double zn = fmin(fmax(v, d.l[i]), d.u[i]);
       const double yn = rh * (v - zn);
@@ -1044,6 +1072,8 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           const double rh = rho_of(d.rtype[i], rho_bar);
           d.rho[i] = rh;
           d.rho_inv[i] = 1.0 / rh;
+          d.rhoT[i] = T(rh);
+          d.rho_invT[i] = T(1.0 / rh);
           wm[i] = rh * z[i] - y[i];
           um[i] = rh * (z[i] - zt[i]) - y[i];
         }

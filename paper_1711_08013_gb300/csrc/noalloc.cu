@@ -86,7 +86,7 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   const size_t tmpn = nkn > na ? nkn : na;
   const size_t ch_kn = nkn / kChunk + nkn / 257 + 1, lr_kn = nkn / 257 + 1;
   const size_t ch_a = na / kChunk + na / 257 + 1, lr_a = na / 257 + 1;
-  constexpr int kSlots = 96;  // ≥ the number of take() calls below (68)
+  constexpr int kSlots = 96;  // ≥ the number of take() calls below (72)
   size_t o[kSlots];
   int c = 0;
   o[c++] = L.template take<int>(n + 1);       // 0 kn_rp
@@ -114,14 +114,14 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   const int first_m = c;
   for (int k = 0; k < nvec_m; ++k) o[c++] = L.template take<double>(m);
   const int first_tn = c;
-  for (int k = 0; k < 10; ++k) o[c++] = L.template take<T>(n);
+  for (int k = 0; k < 11; ++k) o[c++] = L.template take<T>(n);
   const int at_rt = c;
-  for (int k = 0; k < 3; ++k) o[c++] = L.template take<T>(m);
+  for (int k = 0; k < 6; ++k) o[c++] = L.template take<T>(m);
   const int at_sc = c;
   o[c++] = L.template take<Scalars>(1);
   const int at_err = c;
   o[c++] = L.template take<int>(2);
-  static_assert(19 + 15 + 19 + 10 + 3 + 2 <= kSlots, "scratch slot table too small");
+  static_assert(19 + 15 + 19 + 11 + 6 + 2 <= kSlots, "scratch slot table too small");
   if (base && p) {
     Dev<T>& d = p->d;
     d.n = in.n;
@@ -152,10 +152,10 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
                      &d.ax, &d.adx, &d.azt, &d.z_out, &d.y_out, &d.pcert, &d.zt, &d.wm, &d.um,
                      &d.Einv};
     for (int k = 0; k < nvec_m; ++k) *mv[k] = (double*)(base + o[first_m + k]);
-    T** tv[] = {&d.dinv, &d.b, &d.mr, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1};
-    for (int k = 0; k < 10; ++k) *tv[k] = (T*)(base + o[first_tn + k]);
-    T** tmv[] = {&d.rt0, &d.rt1, &d.ap};
-    for (int k = 0; k < 3; ++k) *tmv[k] = (T*)(base + o[at_rt + k]);
+    T** tv[] = {&d.dinv, &d.b, &d.mr, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1, &d.dxt};
+    for (int k = 0; k < 11; ++k) *tv[k] = (T*)(base + o[first_tn + k]);
+    T** tmv[] = {&d.rt0, &d.rt1, &d.ap, &d.dzt, &d.rhoT, &d.rho_invT};
+    for (int k = 0; k < 6; ++k) *tmv[k] = (T*)(base + o[at_rt + k]);
     d.sc = (Scalars*)(base + o[at_sc]);
     p->err = (int*)(base + o[at_err]);
     p->flag = p->err + 1;

@@ -212,8 +212,9 @@ void fill_dev(osqp_solver* s, Arena& A, Dev<T>& d, int4** kn_ch, int** kn_lr, in
   for (double** p : mvec) *p = A.take<double>(m);
   T** tn[] = {&d.dinv, &d.b, &d.mr, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1};
   for (T** p : tn) *p = A.take<T>(n);
-  T** tmv[] = {&d.rt0, &d.rt1, &d.ap};
+  T** tmv[] = {&d.rt0, &d.rt1, &d.ap, &d.dzt, &d.rhoT, &d.rho_invT};
   for (T** p : tmv) *p = A.take<T>(m);
+  d.dxt = A.take<T>(n);
   d.kn.nrows = n;
   d.kn.group = s->kn_s.group;
   d.kn.long_thresh = s->kn_s.long_thresh;
