@@ -101,24 +101,35 @@ struct Bump {
   }
 };
 
-// Static block (uploaded once): structure, raw values, schedules, raw vectors.
-struct StaticOffsets {
-  size_t kn_rp, kn_ci, kn_raw, a_rp, a_ci, a_raw, kn_ch, kn_lr, a_ch, a_lr, q, l, u, end;
+// Static block (uploaded once): sliced structure, raw values, schedules,
+// raw vectors.
+struct SchedOffsets {
+  size_t sl, sr, ch, lr;
 };
+
+struct StaticOffsets {
+  size_t kn_ci, kn_raw, a_ci, a_raw, q, l, u, end;
+  SchedOffsets kn, a;
+};
+
+SchedOffsets sched_offsets(Bump& b, const SchedHost& h) {
+  SchedOffsets o;
+  o.sl = b.take<int2>(h.slices.size());
+  o.sr = b.take<int>(h.srow.size());
+  o.ch = b.take<int4>(h.chunks.size());
+  o.lr = b.take<int>(h.long_rows.size());
+  return o;
+}
 
 StaticOffsets static_offsets(const ProblemLayout& L) {
   Bump b;
   StaticOffsets o;
-  o.kn_rp = b.take<int>(L.n + 1);
-  o.kn_ci = b.take<int>(L.nnz_kn);
-  o.kn_raw = b.take<double>(L.nnz_kn);
-  o.a_rp = b.take<int>(L.m + 1);
-  o.a_ci = b.take<int>(L.nnz_a);
-  o.a_raw = b.take<double>(L.nnz_a);
-  o.kn_ch = b.take<int4>(L.kn_s.chunks.size());
-  o.kn_lr = b.take<int>(L.kn_s.long_rows.size());
-  o.a_ch = b.take<int4>(L.a_s.chunks.size());
-  o.a_lr = b.take<int>(L.a_s.long_rows.size());
+  o.kn_ci = b.take<int>(L.kn_s.npos);
+  o.kn_raw = b.take<double>(L.kn_s.npos);
+  o.a_ci = b.take<int>(L.a_s.npos);
+  o.a_raw = b.take<double>(L.a_s.npos);
+  o.kn = sched_offsets(b, L.kn_s);
+  o.a = sched_offsets(b, L.a_s);
   o.q = b.take<double>(L.n);
   o.l = b.take<double>(L.m);
   o.u = b.take<double>(L.m);
@@ -131,8 +142,8 @@ template <typename T>
 size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
   Bump b;
   const size_t n = L.n, m = L.m;
-  const size_t kn_v = b.take<T>(L.nnz_kn);
-  const size_t a_v = b.take<T>(L.nnz_a);
+  const size_t kn_v = b.take<T>(L.kn_s.npos);
+  const size_t a_v = b.take<T>(L.a_s.npos);
   const size_t rt = b.take<uint8_t>(m);
   size_t on[15], om[19], otn[11], otm[6];
   for (auto& v : on) v = b.take<double>(n);
@@ -212,21 +223,27 @@ void fill_batch_devs(osqp_batch* b) {
     char* sb = b->arena + L.s_off;
     d->n = L.n;
     d->m = L.m;
-    d->kn_rp = (const int*)(sb + o.kn_rp);
     d->kn_ci = (const int*)(sb + o.kn_ci);
     d->kn_raw = (const double*)(sb + o.kn_raw);
-    d->a_rp = (const int*)(sb + o.a_rp);
     d->a_ci = (const int*)(sb + o.a_ci);
     d->a_raw = (const double*)(sb + o.a_raw);
     d->q_raw = (const double*)(sb + o.q);
     d->l_raw = (const double*)(sb + o.l);
     d->u_raw = (const double*)(sb + o.u);
-    d->kn = Sched{L.n, L.kn_s.group, L.kn_s.long_thresh, (int)L.kn_s.chunks.size(),
-                  (int)L.kn_s.long_rows.size(), (const int4*)(sb + o.kn_ch),
-                  (const int*)(sb + o.kn_lr)};
-    d->as = Sched{L.m, L.a_s.group, L.a_s.long_thresh, (int)L.a_s.chunks.size(),
-                  (int)L.a_s.long_rows.size(), (const int4*)(sb + o.a_ch),
-                  (const int*)(sb + o.a_lr)};
+    auto sched = [&](const SchedHost& h, const SchedOffsets& so, int nrows) {
+      return Sched{nrows,
+                   h.group,
+                   h.long_thresh,
+                   (int)h.chunks.size(),
+                   (int)h.long_rows.size(),
+                   (int)h.slices.size(),
+                   (const int2*)(sb + so.sl),
+                   (const int*)(sb + so.sr),
+                   (const int4*)(sb + so.ch),
+                   (const int*)(sb + so.lr)};
+    };
+    d->kn = sched(L.kn_s, o.kn, L.n);
+    d->as = sched(L.a_s, o.a, L.m);
     dynamic_carve<T>(L, b->arena + L.v_off, d);
   }
 }
@@ -388,27 +405,39 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
     auto put = [&](size_t off, const void* src, size_t bytes) {
       if (bytes) std::memcpy(base + off, src, bytes);
     };
-    put(o.kn_rp, h.kn_rp.data(), sizeof(int) * h.kn_rp.size());
-    put(o.kn_ci, h.kn_ci.data(), sizeof(int) * h.kn_ci.size());
-    put(o.a_rp, h.a_rp.data(), sizeof(int) * h.a_rp.size());
-    put(o.a_ci, h.a_ci.data(), sizeof(int) * h.a_ci.size());
+    // column indices and raw values at their positions; padding: column −1, 0
+    int* knc = reinterpret_cast<int*>(base + o.kn_ci);
     double* knr = reinterpret_cast<double*>(base + o.kn_raw);
+    std::fill(knc, knc + L.kn_s.npos, -1);
     for (int k = 0; k < h.nnz_kn; ++k) {
-      const int src = h.kn_src[k];
-      knr[k] = src < h.nnz_p ? P[i].val[src] : A[i].val[src - h.nnz_p];
+      const int at = L.kn_s.pos[k], src = h.kn_src[k];
+      knc[at] = h.kn_ci[k];
+      knr[at] = src < h.nnz_p ? P[i].val[src] : A[i].val[src - h.nnz_p];
     }
+    int* ac = reinterpret_cast<int*>(base + o.a_ci);
     double* ar = reinterpret_cast<double*>(base + o.a_raw);
-    for (int k = 0; k < h.nnz_a; ++k) ar[k] = A[i].val[h.a_src[k] - h.nnz_p];
-    put(o.kn_ch, L.kn_s.chunks.data(), sizeof(int4) * L.kn_s.chunks.size());
-    put(o.kn_lr, L.kn_s.long_rows.data(), sizeof(int) * L.kn_s.long_rows.size());
-    put(o.a_ch, L.a_s.chunks.data(), sizeof(int4) * L.a_s.chunks.size());
-    put(o.a_lr, L.a_s.long_rows.data(), sizeof(int) * L.a_s.long_rows.size());
+    std::fill(ac, ac + L.a_s.npos, -1);
+    for (int k = 0; k < h.nnz_a; ++k) {
+      const int at = L.a_s.pos[k];
+      ac[at] = h.a_ci[k];
+      ar[at] = A[i].val[h.a_src[k] - h.nnz_p];
+    }
+    const std::pair<const SchedHost*, const SchedOffsets*> sch[] = {{&L.kn_s, &o.kn},
+                                                                    {&L.a_s, &o.a}};
+    for (const auto& so : sch) {
+      put(so.second->sl, so.first->slices.data(), sizeof(int2) * so.first->slices.size());
+      put(so.second->sr, so.first->srow.data(), sizeof(int) * so.first->srow.size());
+      put(so.second->ch, so.first->chunks.data(), sizeof(int4) * so.first->chunks.size());
+      put(so.second->lr, so.first->long_rows.data(), sizeof(int) * so.first->long_rows.size());
+    }
     put(o.q, q[i], sizeof(double) * L.n);
     if (L.m) {
       put(o.l, l[i], sizeof(double) * L.m);
       put(o.u, u[i], sizeof(double) * L.m);
     }
     hs[i] = HostStructure();  // release host memory early
+    b->L[i].kn_s.pos = {};
+    b->L[i].a_s.pos = {};
   }
   if (!flush(b->static_bytes)) return fail(OSQP_ERR_CUDA);
 

@@ -40,9 +40,18 @@ enum DevStatus : int { kUnsolved = 0, kSolved = 1, kMaxIter = 2, kPrimInf = 3, k
                        kTimeLimit = 5, kNumErr = 6 };
 enum DevError : int { kDevOk = 0, kDevBarrierTimeout = 1 };
 
+// Sliced layout of a sparse matrix (rows of Kn = [P̄ Āᵀ] or of Ā).  Rows of
+// at most long_thresh nonzeros, stably sorted by decreasing length, form
+// slices of 32/group rows; a row's nonzeros are dealt to `group` lanes, and
+// step t of a slice stores one nonzero per lane at first + 32·t + lane, so
+// every warp load of column indices or values is one coalesced 128-byte
+// line.  Padding positions hold column −1.  Longer rows follow in CSR order
+// and are split into kChunk-nonzero chunks, each taken by a whole warp.
 struct Sched {
-  int nrows, group, long_thresh, nchunks, nlong;
-  const int4* chunks;   // (row, begin, end, first-chunk-of-row)
+  int nrows, group, long_thresh, nchunks, nlong, nslices;
+  const int2* slices;   // (first position, steps)
+  const int* srow;      // row of local row r of slice s at s·(32/group) + r; −1 = none
+  const int4* chunks;   // (row, begin, end, first-chunk-of-row) in positions
   const int* long_rows;
 };
 
@@ -68,12 +77,10 @@ struct Params {
 template <typename T>
 struct Dev {
   int n, m;
-  const int* kn_rp;
   const int* kn_ci;
   T* kn_v;
   const double* kn_raw;
   Sched kn;
-  const int* a_rp;
   const int* a_ci;
   T* a_v;
   const double* a_raw;
@@ -318,40 +325,53 @@ struct BlockTeam {
   }
 };
 
+// A plain (non-cooperative) launch as a traversal team: no barriers.
+struct PlainTeam {
+  __device__ int nthreads() const { return gridDim.x * blockDim.x; }
+  __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+  __device__ int nwarps() const { return gridDim.x * (blockDim.x >> 5); }
+  __device__ int warp() const { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+};
+
 // ---------------------------------------------------------------------------
-// Scheduled CSR traversal.  gather(col, val, acc) folds one nonzero into the
-// NV accumulators; the group / warp then combines lanes (sum, or max when
-// MAXR) and on_row(row, acc) runs once per short row, on_chunk(row, first,
-// acc) once per long-row chunk.
+// Traversal of the sliced layout.  gather(col, val, acc) folds one nonzero
+// into the NV accumulators; the group then combines its lanes (sum, or max
+// when MAXR) and on_row(row, acc) runs once per short row, on_chunk(row,
+// first, acc) once per long-row chunk.  A lane accumulates its nonzeros of a
+// row in order and the group combines them by a fixed shuffle tree, so a
+// row's result does not depend on where its slice sits.
 // ---------------------------------------------------------------------------
 template <int NV, bool MAXR, typename AT, typename MT, class Team, class G, class R, class C>
-__device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* __restrict__ rp,
-                                     const int* __restrict__ ci, const MT* __restrict__ va,
-                                     G gather, R on_row, C on_chunk) {
+__device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* __restrict__ ci,
+                                     const MT* __restrict__ va, G gather, R on_row, C on_chunk) {
+  constexpr int B = NV == 1 ? 8 : 4;  // steps whose loads are issued together
   const int lane = threadIdx.x & 31;
   const int Gw = S.group;
   const int sub = lane & (Gw - 1);
-  const int gpw = 32 / Gw;
+  const int spw = 32 / Gw;
   const int gw = lane / Gw;
   const unsigned gmask = (Gw == 32) ? 0xffffffffu : (((1u << Gw) - 1u) << (gw * Gw));
-  const int ngroups = tm.nwarps() * gpw;
-  for (int row = tm.warp() * gpw + gw; row < S.nrows; row += ngroups) {
-    const int b = rp[row], e = rp[row + 1];
-    if (e - b > S.long_thresh) continue;
+  for (int s = tm.warp(); s < S.nslices; s += tm.nwarps()) {
+    const int2 sl = S.slices[s];
+    const int row = S.srow[s * spw + gw];
     AT acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = AT(0);
-    int k = b + sub;
-    // four nonzeros per lane per step: their loads are issued together
-    for (; k + 3 * Gw < e; k += 4 * Gw) {
-      const int c0 = ci[k], c1 = ci[k + Gw], c2 = ci[k + 2 * Gw], c3 = ci[k + 3 * Gw];
-      const MT v0 = va[k], v1 = va[k + Gw], v2 = va[k + 2 * Gw], v3 = va[k + 3 * Gw];
-      gather(c0, v0, acc);
-      gather(c1, v1, acc);
-      gather(c2, v2, acc);
-      gather(c3, v3, acc);
+    const int* __restrict__ cp = ci + sl.x + lane;
+    const MT* __restrict__ vp = va + sl.x + lane;
+    for (int t = 0; t < sl.y; t += B) {
+      int cc[B];
+      MT vv[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const bool in = t + u < sl.y;  // uniform across the warp
+        cc[u] = in ? cp[(t + u) * 32] : -1;
+        vv[u] = in ? vp[(t + u) * 32] : MT(0);
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u)
+        if (cc[u] >= 0) gather(cc[u], vv[u], acc);
     }
-    for (; k < e; k += Gw) gather(ci[k], va[k], acc);
     for (int off = Gw >> 1; off > 0; off >>= 1) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -359,7 +379,7 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* 
         acc[v] = MAXR ? (acc[v] > o ? acc[v] : o) : acc[v] + o;
       }
     }
-    if (sub == 0) on_row(row, acc);
+    if (sub == 0 && row >= 0) on_row(row, acc);
   }
   for (int c = tm.warp(); c < S.nchunks; c += tm.nwarps()) {
     const int4 ch = S.chunks[c];
@@ -390,20 +410,21 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* 
   }
 }
 
-// Per-entry pass in schedule order: f(row, k) for every nonzero k of the row.
-template <typename MT, class Team, class F>
+// Per-entry pass: f(row, k) for every stored nonzero k (padding skipped).
+template <class Team, class F>
 __device__ __forceinline__ void foreach_entry(const Team& tm, const Sched& S,
-                                              const int* __restrict__ rp, F f) {
+                                              const int* __restrict__ ci, F f) {
   const int lane = threadIdx.x & 31;
-  const int Gw = S.group;
-  const int sub = lane & (Gw - 1);
-  const int gpw = 32 / Gw;
-  const int gw = lane / Gw;
-  const int ngroups = tm.nwarps() * gpw;
-  for (int row = tm.warp() * gpw + gw; row < S.nrows; row += ngroups) {
-    const int b = rp[row], e = rp[row + 1];
-    if (e - b > S.long_thresh) continue;
-    for (int k = b + sub; k < e; k += Gw) f(row, k);
+  const int spw = 32 / S.group;
+  const int gw = lane / S.group;
+  for (int s = tm.warp(); s < S.nslices; s += tm.nwarps()) {
+    const int2 sl = S.slices[s];
+    const int row = S.srow[s * spw + gw];
+    if (row < 0) continue;
+    for (int t = 0; t < sl.y; ++t) {
+      const int k = sl.x + 32 * t + lane;
+      if (ci[k] >= 0) f(row, k);
+    }
   }
   for (int c = tm.warp(); c < S.nchunks; c += tm.nwarps()) {
     const int4 ch = S.chunks[c];
@@ -439,7 +460,7 @@ __device__ __forceinline__ void jacobi_rows(const Team& tm, const Dev<T>& d, dou
   const int n = d.n;
   const uint8_t* __restrict__ rtype = d.rtype;
   spmv<1, false, double, T>(
-      tm, d.kn, d.kn_rp, d.kn_ci, d.kn_v,
+      tm, d.kn, d.kn_ci, d.kn_v,
       [&](int c, T v, double* acc) {
         if (c >= n) {
           double vv = (double)v;
@@ -494,7 +515,7 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
     // Kn, and for the last m through the rows of Ā.
     const double cc = c;
     spmv<2, true, double, double>(
-        tm, d.kn, d.kn_rp, d.kn_ci, d.kn_raw,
+        tm, d.kn, d.kn_ci, d.kn_raw,
         [&](int col, double v, double* acc) {
           if (col < n) acc[0] = fmax(acc[0], fabs(v) * d.D[col]);
           else acc[1] = fmax(acc[1], fabs(v) * d.E[col - n]);
@@ -504,7 +525,7 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
           atomic_max_nonneg(&d.nrm_n[j], d.D[j] * fmax(cc * acc[0], acc[1]));
         });
     spmv<1, true, double, double>(
-        tm, d.as, d.a_rp, d.a_ci, d.a_raw,
+        tm, d.as, d.a_ci, d.a_raw,
         [&](int col, double v, double* acc) { acc[0] = fmax(acc[0], fabs(v) * d.D[col]); },
         [&](int i, double* acc) { d.nrm_m[i] = d.E[i] * acc[0]; },
         [&](int i, int, double* acc) { atomic_max_nonneg(&d.nrm_m[i], d.E[i] * acc[0]); });
@@ -529,7 +550,7 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
     ++passes;
     // Cost scaling γ = 1/max{mean_j ‖P̄_:,j‖∞, ‖q̄‖∞} with the new D.
     spmv<1, true, double, double>(
-        tm, d.kn, d.kn_rp, d.kn_ci, d.kn_raw,
+        tm, d.kn, d.kn_ci, d.kn_raw,
         [&](int col, double v, double* acc) {
           if (col < n) acc[0] = fmax(acc[0], fabs(v) * d.D[col]);
         },
@@ -554,7 +575,7 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
     if (dev[0] <= P.eps_equil) break;
   }
   // Scaled data: P̄ = cDPD, Ā = EAD (in both Kn and Ā), q̄ = cDq, [El, Eu].
-  foreach_entry<double>(tm, d.kn, d.kn_rp, [&](int j, int k) {
+  foreach_entry(tm, d.kn, d.kn_ci, [&](int j, int k) {
     const int col = d.kn_ci[k];
     const double v = d.kn_raw[k];
     double s;
@@ -566,7 +587,7 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
     }
     d.kn_v[k] = T(s);
   });
-  foreach_entry<double>(tm, d.as, d.a_rp,
+  foreach_entry(tm, d.as, d.a_ci,
                         [&](int i, int k) { d.a_v[k] = T(d.E[i] * d.a_raw[k] * d.D[d.a_ci[k]]); });
   for (int j = tid; j < n; j += nth) {
     d.q[j] = c * d.D[j] * d.q_raw[j];
@@ -652,10 +673,8 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   double rho_bar = d.sc->rho_bar;
   const unsigned long long t_start = gtimer();
   // Pointers read once (restrict-qualified for the compiler).
-  const int* __restrict__ kn_rp = d.kn_rp;
   const int* __restrict__ kn_ci = d.kn_ci;
   const T* __restrict__ kn_v = d.kn_v;
-  const int* __restrict__ a_rp = d.a_rp;
   const int* __restrict__ a_ci = d.a_ci;
   const T* __restrict__ a_v = d.a_v;
   double* __restrict__ x = d.x;
@@ -713,7 +732,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     {
       T* __restrict__ r = rbuf(cur);
       spmv<2, false, double, T>(
-          tm, d.kn, kn_rp, kn_ci, kn_v,
+          tm, d.kn, kn_ci, kn_v,
           [&](int col, T v, double* acc) {
             const double vv = (double)v;
             if (col < n) {
@@ -760,7 +779,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       red3[1] = (double)a1;
       red3[2] = (double)a2;
       spmv<1, false, T, T>(
-          tm, d.as, a_rp, a_ci, a_v,
+          tm, d.as, a_ci, a_v,
           [&](int col, T v, T* acc) { acc[0] += v * (r[col] * dinv[col]); },
           [&](int i, T* acc) { t[i] = rhoT[i] * acc[0]; },
           [&](int i, int, T* acc) { atomicAdd(&t[i], rhoT[i] * acc[0]); });
@@ -783,7 +802,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       T* __restrict__ w = wbuf(cur);
       const T* __restrict__ tg = tbuf(cur);
       spmv<1, false, T, T>(
-          tm, d.kn, kn_rp, kn_ci, kn_v,
+          tm, d.kn, kn_ci, kn_v,
           [&](int col, T v, T* acc) { acc[0] += v * (col < n ? u[col] : tg[col - n]); },
           [&](int j, T* acc) {
             const T wj = T(sigma) * u[j] + acc[0];
@@ -839,7 +858,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       {
         T* __restrict__ tn = tbuf(nxt);
         spmv<1, false, T, T>(
-            tm, d.as, a_rp, a_ci, a_v, [&](int col, T v, T* acc) { acc[0] += v * u[col]; },
+            tm, d.as, a_ci, a_v, [&](int col, T v, T* acc) { acc[0] += v * u[col]; },
             [&](int i, T* acc) { tn[i] = rhoT[i] * acc[0]; },
             [&](int i, int, T* acc) { atomicAdd(&tn[i], rhoT[i] * acc[0]); });
       }
@@ -859,7 +878,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         }
         const T* __restrict__ tg = tbuf(nxt);
         spmv<1, false, T, T>(
-            tm, d.kn, kn_rp, kn_ci, kn_v,
+            tm, d.kn, kn_ci, kn_v,
             [&](int col, T v, T* acc) { acc[0] += v * (col < n ? u[col] : tg[col - n]); },
             [&](int j, T* acc) {
               const T wj = T(sigma) * u[j] + acc[0];
@@ -936,7 +955,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       const double* __restrict__ dxp = d.dx;
       const double* __restrict__ dyp = d.dy;
       spmv<4, false, double, T>(
-          tm, d.kn, kn_rp, kn_ci, kn_v,
+          tm, d.kn, kn_ci, kn_v,
           [&](int col, T v, double* acc) {
             const double vv = (double)v;
             if (col < n) {
@@ -964,7 +983,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
             atomicAdd(&d.atdy[j], acc[3]);
           });
       spmv<3, false, double, T>(
-          tm, d.as, a_rp, a_ci, a_v,
+          tm, d.as, a_ci, a_v,
           [&](int col, T v, double* acc) {
             const double vv = (double)v;
             acc[0] += vv * x[col];

@@ -18,16 +18,20 @@ namespace host {
 
 // Row schedule from row-length statistics.  Rows longer than
 // max(256, 8·mean) are split into kChunk-nonzero chunks handled by whole
-// warps.  The sub-warp width G for the other rows is the largest power of two
+// warps.  The group width G for the other rows is the largest power of two
 // that still gives every group about one row (32·warps/rows), kept between
 // the width that caps a lane at 16 nonzeros of a mean row and the smallest
-// power of two ≥ the mean row length.  (A wider G would coalesce more of the
-// gathers, but on GB300 the serial chain of dependent loads per group costs
-// more: measured on the Lasso, portfolio, random-QP and MPC workloads.)
+// power of two ≥ the mean row length.  (A wider G would spread a row over
+// more lanes, but on GB300 the serial chain of dependent loads per group
+// costs more: measured on the Lasso, portfolio, random-QP and MPC
+// workloads.)  The short rows are then laid out in slices (see Sched).
 struct SchedHost {
-  int group = 1, long_thresh = 256;
+  int group = 1, long_thresh = 256, npos = 0;
+  std::vector<int2> slices;
+  std::vector<int> srow;
   std::vector<int4> chunks;
   std::vector<int> long_rows;
+  std::vector<int> pos;  // CSR index → position in the sliced layout
 };
 
 inline int sched_group(double mean_short, long long nshort, long long nwarps) {
@@ -46,22 +50,60 @@ inline SchedHost make_sched(const std::vector<int>& rp, long long nwarps) {
   const long long nnz = nrows > 0 ? rp[nrows] : 0;
   const double mean_all = nrows > 0 ? (double)nnz / nrows : 0.0;
   S.long_thresh = std::max(256, (int)(8.0 * std::ceil(mean_all)));
+  std::vector<int> shortr;
   long long sn = 0;
-  long long scount = 0;
   for (int r = 0; r < nrows; ++r) {
     const int len = rp[r + 1] - rp[r];
     if (len <= S.long_thresh) {
       sn += len;
-      ++scount;
+      shortr.push_back(r);
     } else {
       S.long_rows.push_back(r);
-      for (int b = rp[r]; b < rp[r + 1]; b += kChunk)
-        S.chunks.push_back(make_int4(r, b, std::min(b + kChunk, rp[r + 1]), b == rp[r] ? 1 : 0));
     }
   }
+  const long long scount = (long long)shortr.size();
   const double ms = scount ? (double)sn / (double)scount : 1.0;
   S.group = sched_group(ms, scount, nwarps);
+  const int G = S.group, spw = 32 / G;
+  std::stable_sort(shortr.begin(), shortr.end(),
+                   [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+  S.pos.assign(nnz, -1);
+  const int nsl = (int)((scount + spw - 1) / spw);
+  S.srow.assign((size_t)nsl * spw, -1);
+  int p = 0;
+  for (int sl = 0; sl < nsl; ++sl) {
+    int W = 0;
+    for (int r = 0; r < spw && sl * spw + r < scount; ++r) {
+      const int row = shortr[sl * spw + r];
+      S.srow[sl * spw + r] = row;
+      W = std::max(W, (rp[row + 1] - rp[row] + G - 1) / G);
+    }
+    S.slices.push_back(make_int2(p, W));
+    for (int r = 0; r < spw; ++r) {
+      const int row = S.srow[sl * spw + r];
+      if (row < 0) continue;
+      for (int j = 0; j < rp[row + 1] - rp[row]; ++j) S.pos[rp[row] + j] = p + 32 * (j / G) + r * G + j % G;
+    }
+    p += 32 * W;
+  }
+  for (int r : S.long_rows) {
+    for (int b = rp[r]; b < rp[r + 1]; b += kChunk) {
+      const int e = std::min(b + kChunk, rp[r + 1]);
+      S.chunks.push_back(make_int4(r, p + (b - rp[r]), p + (e - rp[r]), b == rp[r] ? 1 : 0));
+    }
+    for (int k = rp[r]; k < rp[r + 1]; ++k) S.pos[k] = p + (k - rp[r]);
+    p += rp[r + 1] - rp[r];
+  }
+  S.npos = p;
   return S;
+}
+
+// v in CSR order → the sliced layout (fill at padding positions).
+template <typename V>
+std::vector<V> to_positions(const SchedHost& S, const std::vector<V>& v, V fill) {
+  std::vector<V> out(S.npos, fill);
+  for (size_t k = 0; k < v.size(); ++k) out[S.pos[k]] = v[k];
+  return out;
 }
 
 struct Arena {

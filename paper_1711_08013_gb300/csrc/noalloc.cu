@@ -6,9 +6,10 @@
 // forbid cudaMalloc/cudaFree after start-up.  For them this entry point runs
 // the same one-CTA solver as osqp_setup/osqp_solve with launch = 1 (Ruiz
 // scaling, ρ and Jacobi, Algorithm 1 with PCG, termination, unscaling), but
-// every intermediate array — including the CSR structure that osqp_setup
-// builds on the host — lives in one file-scope device array of
-// kNoallocScratchBytes.  The caller passes device inputs and outputs.
+// every intermediate array — including the CSR structure and the sliced
+// layout that osqp_setup builds on the host — lives in one file-scope device
+// array of kNoallocScratchBytes.  The caller passes device inputs and
+// outputs.
 //
 // The array is statically allocated in every GPU that loads the library and
 // stays there until the process exits.  Its device address is looked up once
@@ -33,11 +34,12 @@ namespace {
 
 constexpr size_t kNoallocScratchBytes = OSQP_NOALLOC_SCRATCH_BYTES;
 constexpr int kNoallocMaxRow = 8192;  // rows longer than this are rejected (sort cost)
+constexpr int kMaxBins = 16384;       // short-row lengths the layout sort can bin
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-enum : int { kNaOk = 0, kNaBadCsc = 1, kNaLongRow = 2 };
+enum : int { kNaOk = 0, kNaBadCsc = 1, kNaLongRow = 2, kNaNoRoom = 3 };
 
 struct NaInput {
   int n, m, nnzP, nnzA;
@@ -67,16 +69,33 @@ struct NaLayout {
   }
 };
 
+// Buffers of one matrix's layout build.
+struct NaSched {
+  int* rp;        // CSR row pointer
+  int* cci;       // CSR columns
+  double* craw;   // CSR raw values
+  int2* slices;
+  int* srow;
+  int4* chunks;
+  int* long_rows;
+  int* lpos;      // first position of each long row
+  int* order;     // short rows, stably sorted by decreasing length
+};
+
 template <typename T>
 struct NaPtrs {
   Dev<T> d;
+  NaSched kn, a;
   int *plen, *cur_n, *alen, *cur_m, *tmp_ci, *err, *flag;
+  int *bin_cnt, *bin_rev, *bin_start, *wsum;
   double* tmp_raw;
-  int4 *kn_chunks, *a_chunks;
-  int *kn_long, *a_long;
+  size_t fixed_end;  // first byte after the fixed carve
+  size_t dyn;        // first free byte after the sliced arrays carved so far
 };
 
-// Carve the scratch array; base == nullptr only measures.
+// Carve the scratch array; base == nullptr only measures.  The sliced
+// arrays (column, raw and working values), whose size depends on the
+// structure, are placed after the fixed part by the kernel itself.
 template <typename T>
 __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p) {
   NaLayout<T> L;
@@ -86,28 +105,39 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   const size_t tmpn = nkn > na ? nkn : na;
   const size_t ch_kn = nkn / kChunk + nkn / 257 + 1, lr_kn = nkn / 257 + 1;
   const size_t ch_a = na / kChunk + na / 257 + 1, lr_a = na / 257 + 1;
-  constexpr int kSlots = 96;  // ≥ the number of take() calls below (72)
+  const size_t nr = n > m ? n : m;
+  constexpr int kSlots = 96;  // ≥ the number of take() calls below (82)
   size_t o[kSlots];
   int c = 0;
-  o[c++] = L.template take<int>(n + 1);       // 0 kn_rp
-  o[c++] = L.template take<int>(nkn);         // 1 kn_ci
-  o[c++] = L.template take<T>(nkn);           // 2 kn_v
-  o[c++] = L.template take<double>(nkn);      // 3 kn_raw
-  o[c++] = L.template take<int>(m + 1);       // 4 a_rp
-  o[c++] = L.template take<int>(na);          // 5 a_ci
-  o[c++] = L.template take<T>(na);            // 6 a_v
-  o[c++] = L.template take<double>(na);       // 7 a_raw
-  o[c++] = L.template take<int>(tmpn);        // 8 tmp_ci
-  o[c++] = L.template take<double>(tmpn);     // 9 tmp_raw
-  o[c++] = L.template take<int>(n);           // 10 plen
-  o[c++] = L.template take<int>(n);           // 11 cur_n
-  o[c++] = L.template take<int>(m);           // 12 alen
-  o[c++] = L.template take<int>(m);           // 13 cur_m
-  o[c++] = L.template take<int4>(ch_kn);      // 14 kn chunks
-  o[c++] = L.template take<int>(lr_kn);       // 15 kn long rows
-  o[c++] = L.template take<int4>(ch_a);       // 16 a chunks
-  o[c++] = L.template take<int>(lr_a);        // 17 a long rows
-  o[c++] = L.template take<uint8_t>(m);       // 18 rtype
+  o[c++] = L.template take<int>(n + 1);       // 0 kn rp
+  o[c++] = L.template take<int>(nkn);         // 1 kn CSR columns
+  o[c++] = L.template take<double>(nkn);      // 2 kn CSR raw
+  o[c++] = L.template take<int>(m + 1);       // 3 a rp
+  o[c++] = L.template take<int>(na);          // 4 a CSR columns
+  o[c++] = L.template take<double>(na);       // 5 a CSR raw
+  o[c++] = L.template take<int>(tmpn);        // 6 tmp_ci
+  o[c++] = L.template take<double>(tmpn);     // 7 tmp_raw
+  o[c++] = L.template take<int>(n);           // 8 plen
+  o[c++] = L.template take<int>(n);           // 9 cur_n
+  o[c++] = L.template take<int>(m);           // 10 alen
+  o[c++] = L.template take<int>(m);           // 11 cur_m
+  o[c++] = L.template take<int4>(ch_kn);      // 12 kn chunks
+  o[c++] = L.template take<int>(lr_kn);       // 13 kn long rows
+  o[c++] = L.template take<int>(lr_kn);       // 14 kn long-row positions
+  o[c++] = L.template take<int4>(ch_a);       // 15 a chunks
+  o[c++] = L.template take<int>(lr_a);        // 16 a long rows
+  o[c++] = L.template take<int>(lr_a);        // 17 a long-row positions
+  o[c++] = L.template take<int2>(n + 1);      // 18 kn slices
+  o[c++] = L.template take<int>(n + 32);      // 19 kn slice rows
+  o[c++] = L.template take<int>(n);           // 20 kn order
+  o[c++] = L.template take<int2>(m + 1);      // 21 a slices
+  o[c++] = L.template take<int>(m + 32);      // 22 a slice rows
+  o[c++] = L.template take<int>(m);           // 23 a order
+  o[c++] = L.template take<int>(kMaxBins + 1);  // 24 bin counts
+  o[c++] = L.template take<int>(kMaxBins + 1);  // 25 bin counts, longest first
+  o[c++] = L.template take<int>(kMaxBins + 2);  // 26 bin starts
+  o[c++] = L.template take<int>(nr + 2);      // 27 slice widths / starts
+  o[c++] = L.template take<uint8_t>(m);       // 28 rtype
   const int nvec_n = 15, nvec_m = 19;
   const int first_n = c;
   for (int k = 0; k < nvec_n; ++k) o[c++] = L.template take<double>(n);
@@ -121,30 +151,28 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   o[c++] = L.template take<Scalars>(1);
   const int at_err = c;
   o[c++] = L.template take<int>(2);
-  static_assert(19 + 15 + 19 + 11 + 6 + 2 <= kSlots, "scratch slot table too small");
+  static_assert(29 + 15 + 19 + 11 + 6 + 2 <= kSlots, "scratch slot table too small");
   if (base && p) {
     Dev<T>& d = p->d;
     d.n = in.n;
     d.m = in.m;
-    d.kn_rp = (const int*)(base + o[0]);
-    d.kn_ci = (const int*)(base + o[1]);
-    d.kn_v = (T*)(base + o[2]);
-    d.kn_raw = (const double*)(base + o[3]);
-    d.a_rp = (const int*)(base + o[4]);
-    d.a_ci = (const int*)(base + o[5]);
-    d.a_v = (T*)(base + o[6]);
-    d.a_raw = (const double*)(base + o[7]);
-    p->tmp_ci = (int*)(base + o[8]);
-    p->tmp_raw = (double*)(base + o[9]);
-    p->plen = (int*)(base + o[10]);
-    p->cur_n = (int*)(base + o[11]);
-    p->alen = (int*)(base + o[12]);
-    p->cur_m = (int*)(base + o[13]);
-    p->kn_chunks = (int4*)(base + o[14]);
-    p->kn_long = (int*)(base + o[15]);
-    p->a_chunks = (int4*)(base + o[16]);
-    p->a_long = (int*)(base + o[17]);
-    d.rtype = (uint8_t*)(base + o[18]);
+    p->kn = NaSched{(int*)(base + o[0]),   (int*)(base + o[1]),   (double*)(base + o[2]),
+                    (int2*)(base + o[18]), (int*)(base + o[19]),  (int4*)(base + o[12]),
+                    (int*)(base + o[13]),  (int*)(base + o[14]),  (int*)(base + o[20])};
+    p->a = NaSched{(int*)(base + o[3]),   (int*)(base + o[4]),   (double*)(base + o[5]),
+                   (int2*)(base + o[21]), (int*)(base + o[22]),  (int4*)(base + o[15]),
+                   (int*)(base + o[16]),  (int*)(base + o[17]),  (int*)(base + o[23])};
+    p->tmp_ci = (int*)(base + o[6]);
+    p->tmp_raw = (double*)(base + o[7]);
+    p->plen = (int*)(base + o[8]);
+    p->cur_n = (int*)(base + o[9]);
+    p->alen = (int*)(base + o[10]);
+    p->cur_m = (int*)(base + o[11]);
+    p->bin_cnt = (int*)(base + o[24]);
+    p->bin_rev = (int*)(base + o[25]);
+    p->bin_start = (int*)(base + o[26]);
+    p->wsum = (int*)(base + o[27]);
+    d.rtype = (uint8_t*)(base + o[28]);
     double** nv[] = {&d.D, &d.q, &d.pdiag, &d.dg, &d.nrm_n, &d.x, &d.dx, &d.px,
                      &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt, &d.Dinv};
     for (int k = 0; k < nvec_n; ++k) *nv[k] = (double*)(base + o[first_n + k]);
@@ -159,6 +187,7 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
     d.sc = (Scalars*)(base + o[at_sc]);
     p->err = (int*)(base + o[at_err]);
     p->flag = p->err + 1;
+    p->fixed_end = L.total;
     // the caller's inputs are read in place; x and y are written in place
     d.q_raw = in.q;
     d.l_raw = in.l;
@@ -167,6 +196,14 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
     d.y_out = in.y;
   }
   return L.total;
+}
+
+// Bytes of the sliced arrays of one matrix with npos positions.
+template <typename T>
+__host__ __device__ size_t sliced_bytes(size_t npos) {
+  const size_t c = npos ? npos : 1;
+  return ((c * sizeof(int) + 255) & ~(size_t)255) + ((c * sizeof(double) + 255) & ~(size_t)255) +
+         ((c * sizeof(T) + 255) & ~(size_t)255);
 }
 
 // Exclusive prefix sum of v[0..count) into out[0..count] by one CTA.
@@ -203,16 +240,24 @@ __device__ void block_exclusive_scan(const int* v, int* out, int count, int* sh)
   __syncthreads();
 }
 
-// Row schedule built on the device (same rule as the host builder of
-// osqp_setup: long rows > max(256, 8·mean) cut into kChunk chunks, sub-warp
-// width = smallest power of two ≥ the mean short-row length).
-__device__ void build_sched(Sched& S, const int* rp, int nrows, int4* chunks, int* long_rows,
-                            int* sh_int, double* sm) {
+// Sliced layout of one CSR matrix, built by one CTA: the layout the host
+// builder of osqp_setup makes (same long-row threshold and group width, short
+// rows stably sorted by decreasing length by a counting sort), so a solve
+// here takes the same arithmetic path as osqp_solve with launch = 1.  The
+// column, raw and working-value arrays are carved at sp.dyn; a layout that
+// does not fit in the scratch array sets kNaNoRoom.
+template <typename T>
+__device__ bool build_sliced(Sched& S, const NaSched& B, NaPtrs<T>& sp, int nrows, char* base,
+                             const int** ci_out, const double** raw_out, T** v_out, int* sh_int,
+                             double* sm) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  const int* rp = B.rp;
   const int nnz = rp[nrows];
   const double mean_all = nrows > 0 ? (double)nnz / nrows : 0.0;
   const int thresh = max(256, (int)(8.0 * ceil(mean_all)));
   double red[2] = {0.0, 0.0};  // short nnz, short rows
-  for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+  for (int r = tid; r < nrows; r += nth) {
     const int len = rp[r + 1] - rp[r];
     if (len <= thresh) {
       red[0] += len;
@@ -222,19 +267,11 @@ __device__ void build_sched(Sched& S, const int* rp, int nrows, int4* chunks, in
   block_reduce<2, 0u>(red, sm);
   const double sn = sm[32 * kMaxRed], sc = sm[32 * kMaxRed + 1];
   __syncthreads();
-  // long rows and their chunks, in row order, by one thread (few long rows)
-  if (threadIdx.x == 0) {
-    int nl = 0, nc = 0;
-    for (int r = 0; r < nrows; ++r) {
-      const int b = rp[r], e = rp[r + 1];
-      if (e - b <= thresh) continue;
-      long_rows[nl++] = r;
-      for (int k = b; k < e; k += kChunk) chunks[nc++] = make_int4(r, k, min(k + kChunk, e), k == b);
-    }
-    sh_int[0] = nl;
-    sh_int[1] = nc;
+  if (thresh > kMaxBins) {
+    if (tid == 0) atomicExch(sp.err, kNaNoRoom);
+    __syncthreads();
+    return false;
   }
-  __syncthreads();
   const double ms = sc > 0 ? sn / sc : 1.0;
   // same width rule as the host schedule builder of osqp_setup
   int g_mean = 1;
@@ -242,19 +279,130 @@ __device__ void build_sched(Sched& S, const int* rp, int nrows, int4* chunks, in
   int g_min = 1;
   while (g_min < 32 && (double)g_min * 16.0 < ms) g_min <<= 1;
   int g_occ = 1;
-  const long long nshort = (long long)sc, nwarps = blockDim.x / 32;
-  while (g_occ < 32 && (long long)(g_occ * 2) * nshort <= 32LL * nwarps) g_occ <<= 1;
+  const long long nshort_ll = (long long)sc, nwarps = nw;
+  while (g_occ < 32 && (long long)(g_occ * 2) * nshort_ll <= 32LL * nwarps) g_occ <<= 1;
   const int G = max(g_min, min(g_mean, g_occ));
-  if (threadIdx.x == 0) {
-    S.nrows = nrows;
-    S.group = G;
-    S.long_thresh = thresh;
-    S.nlong = sh_int[0];
-    S.nchunks = sh_int[1];
-    S.chunks = chunks;
-    S.long_rows = long_rows;
+  const int spw = 32 / G;
+  const int nshort = (int)sc;
+  // counting sort of the short rows by decreasing length, stable in the row
+  // index: bin starts from a scan of the counts taken longest first
+  const int nb = thresh + 1;
+  for (int i = tid; i < nb; i += nth) sp.bin_cnt[i] = 0;
+  __syncthreads();
+  for (int r = tid; r < nrows; r += nth) {
+    const int len = rp[r + 1] - rp[r];
+    if (len <= thresh) atomicAdd(&sp.bin_cnt[len], 1);
   }
   __syncthreads();
+  for (int i = tid; i < nb; i += nth) sp.bin_rev[i] = sp.bin_cnt[thresh - i];
+  __syncthreads();
+  block_exclusive_scan(sp.bin_rev, sp.bin_start, nb, sh_int);
+  for (int i = tid; i < nb; i += nth) sp.bin_cnt[i] = 0;
+  __syncthreads();
+  // rows in index order, one CTA-wide chunk at a time; within a chunk the
+  // warps take their turn so that equal lengths keep their index order
+  for (int r0 = 0; r0 < nrows; r0 += nth) {
+    const int r = r0 + tid;
+    int len = -1;
+    if (r < nrows) {
+      const int l = rp[r + 1] - rp[r];
+      if (l <= thresh) len = l;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, len);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const bool leader = (__ffs(peers) - 1) == lane;
+    for (int w = 0; w < nw; ++w) {
+      if (wid == w) {
+        int at = 0;
+        if (len >= 0) at = sp.bin_start[thresh - len] + sp.bin_cnt[len] + rank;
+        __syncwarp();
+        if (len >= 0) {
+          if (leader) sp.bin_cnt[len] += __popc(peers);
+          B.order[at] = r;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // slices: widths from their first (longest) row, starts by a scan
+  const int nsl = (nshort + spw - 1) / spw;
+  for (int q = tid; q < nsl; q += nth) {
+    const int r = B.order[q * spw];
+    sp.wsum[q] = 32 * ((rp[r + 1] - rp[r] + G - 1) / G);
+  }
+  __syncthreads();
+  block_exclusive_scan(sp.wsum, sp.wsum, nsl, sh_int);
+  for (int q = tid; q < nsl; q += nth)
+    B.slices[q] = make_int2(sp.wsum[q], (sp.wsum[q + 1] - sp.wsum[q]) / 32);
+  for (int q = tid; q < nsl * spw; q += nth) B.srow[q] = q < nshort ? B.order[q] : -1;
+  // long rows in row order after the slices, with their chunks (few long
+  // rows: one thread), then the sliced arrays
+  if (tid == 0) {
+    int nl = 0, nc = 0, p = sp.wsum[nsl];
+    for (int r = 0; r < nrows; ++r) {
+      const int b = rp[r], e = rp[r + 1];
+      if (e - b <= thresh) continue;
+      B.long_rows[nl] = r;
+      B.lpos[nl] = p;
+      ++nl;
+      for (int k = b; k < e; k += kChunk)
+        B.chunks[nc++] = make_int4(r, p + (k - b), p + (min(k + kChunk, e) - b), k == b);
+      p += e - b;
+    }
+    const size_t np = p;
+    size_t off = (sp.dyn + 255) & ~(size_t)255;
+    const size_t at_ci = off;
+    off = (off + (np ? np : 1) * sizeof(int) + 255) & ~(size_t)255;
+    const size_t at_raw = off;
+    off = (off + (np ? np : 1) * sizeof(double) + 255) & ~(size_t)255;
+    const size_t at_v = off;
+    off += (np ? np : 1) * sizeof(T);
+    if (off > kNoallocScratchBytes) {
+      atomicExch(sp.err, kNaNoRoom);
+    } else {
+      sp.dyn = off;
+      *ci_out = (const int*)(base + at_ci);
+      *raw_out = (const double*)(base + at_raw);
+      *v_out = (T*)(base + at_v);
+      S.nrows = nrows;
+      S.group = G;
+      S.long_thresh = thresh;
+      S.nlong = nl;
+      S.nchunks = nc;
+      S.nslices = nsl;
+      S.slices = B.slices;
+      S.srow = B.srow;
+      S.chunks = B.chunks;
+      S.long_rows = B.long_rows;
+    }
+  }
+  __syncthreads();
+  if (*(volatile int*)sp.err != kNaOk) return false;
+  int* ci = (int*)*ci_out;
+  double* raw = (double*)*raw_out;
+  const int pshort = sp.wsum[nsl];
+  for (int q = tid; q < pshort; q += nth) {
+    ci[q] = -1;
+    raw[q] = 0.0;
+  }
+  __syncthreads();
+  for (int q = tid; q < nshort; q += nth) {
+    const int r = B.order[q], s0 = sp.wsum[q / spw], rr = q % spw;
+    for (int j = 0; j < rp[r + 1] - rp[r]; ++j) {
+      const int at = s0 + 32 * (j / G) + rr * G + j % G;
+      ci[at] = B.cci[rp[r] + j];
+      raw[at] = B.craw[rp[r] + j];
+    }
+  }
+  for (int q = wid; q < S.nlong; q += nw) {
+    const int r = B.long_rows[q], b = rp[r], p0 = B.lpos[q];
+    for (int j = lane; j < rp[r + 1] - b; j += 32) {
+      ci[p0 + j] = B.cci[b + j];
+      raw[p0 + j] = B.craw[b + j];
+    }
+  }
+  __syncthreads();
+  return true;
 }
 
 // Column of CSC entry k (binary search in colptr).
@@ -323,9 +471,9 @@ __global__ void __launch_bounds__(kThreads) k_noalloc(NaInput in, const __grid_c
   __syncthreads();
   for (int j = tid; j < n; j += nth) sp.cur_n[j] = sp.plen[j] + (in.Ap[j + 1] - in.Ap[j]);
   __syncthreads();
-  block_exclusive_scan(sp.cur_n, (int*)d.kn_rp, n, sh_int);
+  block_exclusive_scan(sp.cur_n, sp.kn.rp, n, sh_int);
   for (int j = tid; j < n; j += nth) {
-    sp.cur_n[j] = d.kn_rp[j];
+    sp.cur_n[j] = sp.kn.rp[j];
     if (sp.plen[j] > kNoallocMaxRow) atomicExch(sp.err, kNaLongRow);
   }
   __syncthreads();
@@ -342,9 +490,9 @@ __global__ void __launch_bounds__(kThreads) k_noalloc(NaInput in, const __grid_c
   }
   for (int k = tid; k < in.nnzA; k += nth) {
     const int j = col_of(in.Ap, n, k);
-    const int pos = d.kn_rp[j] + sp.plen[j] + (k - in.Ap[j]);
-    ((int*)d.kn_ci)[pos] = n + in.Ai[k];
-    ((double*)d.kn_raw)[pos] = in.Ax[k];
+    const int pos = sp.kn.rp[j] + sp.plen[j] + (k - in.Ap[j]);
+    sp.kn.cci[pos] = n + in.Ai[k];
+    sp.kn.craw[pos] = in.Ax[k];
   }
   __syncthreads();
   if (*(volatile int*)sp.err != kNaOk) {
@@ -352,23 +500,23 @@ __global__ void __launch_bounds__(kThreads) k_noalloc(NaInput in, const __grid_c
     return;
   }
   // rank sort of each row's P part by column (unique columns → unique order)
-  for (int e = tid; e < d.kn_rp[n]; e += nth) {
-    const int r = col_of(d.kn_rp, n, e);
-    const int b = d.kn_rp[r], len = sp.plen[r];
+  for (int e = tid; e < sp.kn.rp[n]; e += nth) {
+    const int r = col_of(sp.kn.rp, n, e);
+    const int b = sp.kn.rp[r], len = sp.plen[r];
     if (e - b >= len) continue;
     const int c = sp.tmp_ci[e];
     int rank = 0;
     for (int f = b; f < b + len; ++f) rank += sp.tmp_ci[f] < c;
-    ((int*)d.kn_ci)[b + rank] = c;
-    ((double*)d.kn_raw)[b + rank] = sp.tmp_raw[e];
+    sp.kn.cci[b + rank] = c;
+    sp.kn.craw[b + rank] = sp.tmp_raw[e];
   }
   __syncthreads();
   // --- Ā rows: counting + atomic scatter + rank sort
   for (int k = tid; k < in.nnzA; k += nth) atomicAdd(&sp.alen[in.Ai[k]], 1);
   __syncthreads();
-  block_exclusive_scan(sp.alen, (int*)d.a_rp, m, sh_int);
+  block_exclusive_scan(sp.alen, sp.a.rp, m, sh_int);
   for (int i = tid; i < m; i += nth) {
-    sp.cur_m[i] = d.a_rp[i];
+    sp.cur_m[i] = sp.a.rp[i];
     if (sp.alen[i] > kNoallocMaxRow) atomicExch(sp.err, kNaLongRow);
   }
   __syncthreads();
@@ -384,19 +532,23 @@ __global__ void __launch_bounds__(kThreads) k_noalloc(NaInput in, const __grid_c
   }
   __syncthreads();
   for (int e = tid; e < in.nnzA; e += nth) {
-    const int r = col_of(d.a_rp, m, e);
-    const int b = d.a_rp[r], len = d.a_rp[r + 1] - b;
+    const int r = col_of(sp.a.rp, m, e);
+    const int b = sp.a.rp[r], len = sp.a.rp[r + 1] - b;
     const int c = sp.tmp_ci[e];
     int rank = 0;
     for (int f = b; f < b + len; ++f) rank += sp.tmp_ci[f] < c;
-    ((int*)d.a_ci)[b + rank] = c;
-    ((double*)d.a_raw)[b + rank] = sp.tmp_raw[e];
+    sp.a.cci[b + rank] = c;
+    sp.a.craw[b + rank] = sp.tmp_raw[e];
   }
   __syncthreads();
-  // --- schedules, then the same stages as the one-CTA solver
-  if (tid == 0) sh_int[2] = 0;
-  build_sched(d.kn, d.kn_rp, n, sp.kn_chunks, sp.kn_long, sh_int, sm);
-  build_sched(d.as, d.a_rp, m, sp.a_chunks, sp.a_long, sh_int, sm);
+  // --- sliced layouts, then the same stages as the one-CTA solver
+  if (tid == 0) sp.dyn = sp.fixed_end;
+  __syncthreads();
+  if (!build_sliced(d.kn, sp.kn, sp, n, scratch, &d.kn_ci, &d.kn_raw, &d.kn_v, sh_int, sm) ||
+      !build_sliced(d.as, sp.a, sp, m, scratch, &d.a_ci, &d.a_raw, &d.a_v, sh_int, sm)) {
+    if (tid == 0) d.sc->dev_error = sp.err[0];
+    return;
+  }
   BlockTeam tm{sm};
   if (!scale_stage(tm, d, P, rho0, true)) return;
   admm_stage(tm, d, P);
@@ -443,8 +595,14 @@ extern "C" int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_col
     return OSQP_ERR_SETTINGS;
   NaInput in{n, m, P_nnz, A_nnz, P_colptr, P_rowind, P_val, q, A_colptr, A_rowind, A_val,
              l, u, x, y};
-  const size_t need = s.precision == OSQP_PRECISION_FP64 ? na_carve<double>(in, nullptr, nullptr)
-                                                        : na_carve<float>(in, nullptr, nullptr);
+  // fixed part plus the smallest sliced arrays (no padding); the kernel
+  // checks the exact layout
+  const size_t nkn_min = (size_t)P_nnz + A_nnz, na_min = A_nnz;
+  const size_t need = s.precision == OSQP_PRECISION_FP64
+                          ? na_carve<double>(in, nullptr, nullptr) + sliced_bytes<double>(nkn_min) +
+                                sliced_bytes<double>(na_min) + 512
+                          : na_carve<float>(in, nullptr, nullptr) + sliced_bytes<float>(nkn_min) +
+                                sliced_bytes<float>(na_min) + 512;
   if (need > kNoallocScratchBytes) return OSQP_ERR_LIMIT;
   char* base = nullptr;
   int rc = scratch_address(&base);
@@ -487,7 +645,7 @@ extern "C" int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_col
     return OSQP_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return OSQP_ERR_CUDA;
   if (sc.dev_error == kNaBadCsc) return OSQP_ERR_CSC;
-  if (sc.dev_error == kNaLongRow) return OSQP_ERR_LIMIT;
+  if (sc.dev_error == kNaLongRow || sc.dev_error == kNaNoRoom) return OSQP_ERR_LIMIT;
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->status = sc.status;

@@ -80,11 +80,13 @@ __global__ void __launch_bounds__(kThreads) k_admm_block(const __grid_constant__
   admm_stage(tm, d, P);
 }
 
-// raw value gather: dst[k] = src[idx[k]]
+// raw value gather: dst[k] = src[idx[k]], 0 where idx[k] < 0 (layout padding)
 __global__ void k_gather(double* __restrict__ dst, const int* __restrict__ idx,
                          const double* __restrict__ src, int count) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x)
-    dst[k] = src[idx[k]];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    const int i = idx[k];
+    dst[k] = i >= 0 ? src[i] : 0.0;
+  }
 }
 
 // warm start, part 1: x̄ = D⁻¹x, ȳ = cE⁻¹y, x̃ = x̄, δ = 0
@@ -102,25 +104,25 @@ __global__ void k_warm_xy(const __grid_constant__ Dev<T> d, const double* __rest
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) {
     d.y[i] = yw ? c * yw[i] / d.E[i] : 0.0;
     d.dy[i] = 0.0;
+    d.z[i] = 0.0;
+    d.zt[i] = 0.0;
   }
 }
 
-// warm start, part 2: z̄ = z̃ = Āx̄ (one warp per row)
+// warm start, part 2: z̄ = z̃ = Āx̄ (long rows of z̄, z̃ were zeroed in part 1)
 template <typename T>
 __global__ void k_warm_z(const __grid_constant__ Dev<T> d) {
-  const int lane = threadIdx.x & 31;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int i = w; i < d.m; i += nw) {
-    double acc = 0.0;
-    for (int k = d.a_rp[i] + lane; k < d.a_rp[i + 1]; k += 32)
-      acc += (double)d.a_v[k] * d.x[d.a_ci[k]];
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) {
-      d.z[i] = acc;
-      d.zt[i] = acc;
-    }
-  }
+  PlainTeam tm;
+  spmv<1, false, double, T>(
+      tm, d.as, d.a_ci, d.a_v, [&](int col, T v, double* acc) { acc[0] += (double)v * d.x[col]; },
+      [&](int i, double* acc) {
+        d.z[i] = acc[0];
+        d.zt[i] = acc[0];
+      },
+      [&](int i, int, double* acc) {
+        atomicAdd(&d.z[i], acc[0]);
+        atomicAdd(&d.zt[i], acc[0]);
+      });
 }
 
 template <typename T>
@@ -149,6 +151,8 @@ struct osqp_solver {
   osqp_settings set{};
   Params P{};
   int n = 0, m = 0, nnzP = 0, nnzA = 0, nnzKn = 0;
+  // CSR structure (setup only), then column indices and CSC sources of the
+  // sliced layouts (−1 at padding)
   std::vector<int> kn_rp, kn_ci, kn_src, a_rp, a_ci, a_src;
   SchedHost kn_s, a_s;
   char* arena = nullptr;
@@ -181,24 +185,33 @@ namespace {
     }                                             \
   } while (0)
 
+// Device copy of a schedule: arrays carved from the arena.
+void take_sched(Arena& A, const SchedHost& h, int nrows, Sched& S) {
+  S.nrows = nrows;
+  S.group = h.group;
+  S.long_thresh = h.long_thresh;
+  S.nchunks = (int)h.chunks.size();
+  S.nlong = (int)h.long_rows.size();
+  S.nslices = (int)h.slices.size();
+  S.slices = A.take<int2>(h.slices.size());
+  S.srow = A.take<int>(h.srow.size());
+  S.chunks = A.take<int4>(h.chunks.size());
+  S.long_rows = A.take<int>(h.long_rows.size());
+}
+
 template <typename T>
-void fill_dev(osqp_solver* s, Arena& A, Dev<T>& d, int4** kn_ch, int** kn_lr, int4** a_ch,
-              int** a_lr) {
+void fill_dev(osqp_solver* s, Arena& A, Dev<T>& d) {
   const int n = s->n, m = s->m;
   d.n = n;
   d.m = m;
-  d.kn_rp = A.take<int>(n + 1);
-  d.kn_ci = A.take<int>(s->nnzKn);
-  d.kn_v = A.take<T>(s->nnzKn);
-  d.kn_raw = A.take<double>(s->nnzKn);
-  d.a_rp = A.take<int>(m + 1);
-  d.a_ci = A.take<int>(s->nnzA);
-  d.a_v = A.take<T>(s->nnzA);
-  d.a_raw = A.take<double>(s->nnzA);
-  *kn_ch = A.take<int4>(s->kn_s.chunks.size());
-  *kn_lr = A.take<int>(s->kn_s.long_rows.size());
-  *a_ch = A.take<int4>(s->a_s.chunks.size());
-  *a_lr = A.take<int>(s->a_s.long_rows.size());
+  d.kn_ci = A.take<int>(s->kn_s.npos);
+  d.kn_v = A.take<T>(s->kn_s.npos);
+  d.kn_raw = A.take<double>(s->kn_s.npos);
+  d.a_ci = A.take<int>(s->a_s.npos);
+  d.a_v = A.take<T>(s->a_s.npos);
+  d.a_raw = A.take<double>(s->a_s.npos);
+  take_sched(A, s->kn_s, n, d.kn);
+  take_sched(A, s->a_s, m, d.as);
   d.q_raw = A.take<double>(n);
   d.l_raw = A.take<double>(m);
   d.u_raw = A.take<double>(m);
@@ -215,20 +228,6 @@ void fill_dev(osqp_solver* s, Arena& A, Dev<T>& d, int4** kn_ch, int** kn_lr, in
   T** tmv[] = {&d.rt0, &d.rt1, &d.ap, &d.dzt, &d.rhoT, &d.rho_invT};
   for (T** p : tmv) *p = A.take<T>(m);
   d.dxt = A.take<T>(n);
-  d.kn.nrows = n;
-  d.kn.group = s->kn_s.group;
-  d.kn.long_thresh = s->kn_s.long_thresh;
-  d.kn.nchunks = (int)s->kn_s.chunks.size();
-  d.kn.nlong = (int)s->kn_s.long_rows.size();
-  d.kn.chunks = *kn_ch;
-  d.kn.long_rows = *kn_lr;
-  d.as.nrows = m;
-  d.as.group = s->a_s.group;
-  d.as.long_thresh = s->a_s.long_thresh;
-  d.as.nchunks = (int)s->a_s.chunks.size();
-  d.as.nlong = (int)s->a_s.long_rows.size();
-  d.as.chunks = *a_ch;
-  d.as.long_rows = *a_lr;
 }
 
 template <typename T>
@@ -303,7 +302,7 @@ int launch_warm(osqp_solver* s, const double* xw, const double* yw) {
   Dev<T>& d = dev_of<T>(s);
   k_warm_xy<T><<<64, 256, 0, s->stream>>>(d, xw, yw);
   CK(cudaGetLastError());
-  k_warm_z<T><<<std::max(1, std::min(1024, (s->m + 7) / 8)), 256, 0, s->stream>>>(d);
+  k_warm_z<T><<<std::max(1, std::min(1024, (s->m + 255) / 256)), 256, 0, s->stream>>>(d);
   CK(cudaGetLastError());
   return OSQP_OK;
 }
@@ -362,18 +361,19 @@ void get_raw(osqp_solver* s, double** kn_raw, double** a_raw, double** q, double
   else raw_ptrs<float>(s, kn_raw, a_raw, q, l, u);
 }
 
-// Values of raw_in (CSC order: P upper then A) → CSR orders of Kn and Ā.
+// Values of raw_in (CSC order: P upper then A) → sliced layouts of Kn and Ā.
 int scatter_raw(osqp_solver* s) {
   double *kn_raw, *a_raw, *q, *l, *u;
   get_raw(s, &kn_raw, &a_raw, &q, &l, &u);
-  if (s->nnzKn > 0) {
-    k_gather<<<std::min(4096, (s->nnzKn + 255) / 256), 256, 0, s->stream>>>(kn_raw, s->kn_src_d,
-                                                                             s->raw_in, s->nnzKn);
+  const int nk = s->kn_s.npos, na = s->a_s.npos;
+  if (nk > 0) {
+    k_gather<<<std::min(4096, (nk + 255) / 256), 256, 0, s->stream>>>(kn_raw, s->kn_src_d,
+                                                                       s->raw_in, nk);
     CK(cudaGetLastError());
   }
-  if (s->nnzA > 0) {
-    k_gather<<<std::min(4096, (s->nnzA + 255) / 256), 256, 0, s->stream>>>(a_raw, s->a_src_d,
-                                                                           s->raw_in, s->nnzA);
+  if (na > 0) {
+    k_gather<<<std::min(4096, (na + 255) / 256), 256, 0, s->stream>>>(a_raw, s->a_src_d,
+                                                                       s->raw_in, na);
     CK(cudaGetLastError());
   }
   return OSQP_OK;
@@ -410,12 +410,10 @@ template <typename T>
 size_t arena_bytes_for(osqp_solver* s, size_t part_doubles) {
   Arena A;
   Dev<T> d{};
-  int4 *a, *c;
-  int *b, *e;
-  fill_dev<T>(s, A, d, &a, &b, &c, &e);
+  fill_dev<T>(s, A, d);
   A.take<double>(s->nnzP + s->nnzA);  // raw_in
-  A.take<int>(s->nnzKn);
-  A.take<int>(s->nnzA);
+  A.take<int>(s->kn_s.npos);
+  A.take<int>(s->a_s.npos);
   A.take<double>(s->n);
   A.take<double>(s->m);
   A.take<Barrier>(1);
@@ -429,12 +427,10 @@ template <typename T>
 int carve_and_upload(osqp_solver* s, size_t part_doubles) {
   Arena A{s->arena, 0};
   Dev<T>& d = dev_of<T>(s);
-  int4 *kn_ch, *a_ch;
-  int *kn_lr, *a_lr;
-  fill_dev<T>(s, A, d, &kn_ch, &kn_lr, &a_ch, &a_lr);
+  fill_dev<T>(s, A, d);
   s->raw_in = A.take<double>(s->nnzP + s->nnzA);
-  s->kn_src_d = A.take<int>(s->nnzKn);
-  s->a_src_d = A.take<int>(s->nnzA);
+  s->kn_src_d = A.take<int>(s->kn_s.npos);
+  s->a_src_d = A.take<int>(s->a_s.npos);
   s->x_ws = A.take<double>(s->n);
   s->y_ws = A.take<double>(s->m);
   s->bar = A.take<Barrier>(1);
@@ -446,16 +442,19 @@ int carve_and_upload(osqp_solver* s, size_t part_doubles) {
     if (bytes == 0) return cudaSuccess;
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
   };
-  CK(up((void*)d.kn_rp, s->kn_rp.data(), s->kn_rp.size() * sizeof(int)));
   CK(up((void*)d.kn_ci, s->kn_ci.data(), s->kn_ci.size() * sizeof(int)));
-  CK(up((void*)d.a_rp, s->a_rp.data(), s->a_rp.size() * sizeof(int)));
   CK(up((void*)d.a_ci, s->a_ci.data(), s->a_ci.size() * sizeof(int)));
   CK(up(s->kn_src_d, s->kn_src.data(), s->kn_src.size() * sizeof(int)));
   CK(up(s->a_src_d, s->a_src.data(), s->a_src.size() * sizeof(int)));
-  CK(up(kn_ch, s->kn_s.chunks.data(), s->kn_s.chunks.size() * sizeof(int4)));
-  CK(up(kn_lr, s->kn_s.long_rows.data(), s->kn_s.long_rows.size() * sizeof(int)));
-  CK(up(a_ch, s->a_s.chunks.data(), s->a_s.chunks.size() * sizeof(int4)));
-  CK(up(a_lr, s->a_s.long_rows.data(), s->a_s.long_rows.size() * sizeof(int)));
+  const std::pair<const SchedHost*, const Sched*> sch[] = {{&s->kn_s, &d.kn}, {&s->a_s, &d.as}};
+  for (const auto& hs : sch) {
+    const SchedHost& h = *hs.first;
+    const Sched& S = *hs.second;
+    CK(up((void*)S.slices, h.slices.data(), h.slices.size() * sizeof(int2)));
+    CK(up((void*)S.srow, h.srow.data(), h.srow.size() * sizeof(int)));
+    CK(up((void*)S.chunks, h.chunks.data(), h.chunks.size() * sizeof(int4)));
+    CK(up((void*)S.long_rows, h.long_rows.data(), h.long_rows.size() * sizeof(int)));
+  }
   CK(cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->stream));
   return OSQP_OK;
 }
@@ -597,6 +596,12 @@ int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const 
     const long long nwarps = (long long)(s->use_grid ? s->grid : 1) * (kThreads / 32);
     s->kn_s = make_sched(s->kn_rp, nwarps);
     s->a_s = make_sched(s->a_rp, nwarps);
+    s->kn_ci = to_positions(s->kn_s, s->kn_ci, -1);
+    s->kn_src = to_positions(s->kn_s, s->kn_src, -1);
+    s->a_ci = to_positions(s->a_s, s->a_ci, -1);
+    s->a_src = to_positions(s->a_s, s->a_src, -1);
+    s->kn_s.pos = {};
+    s->a_s.pos = {};
   }
   const size_t part_doubles = (size_t)2 * s->grid * kMaxRed;
   const size_t bytes = settings->precision == OSQP_PRECISION_FP64
