@@ -25,7 +25,7 @@ using namespace osqpgb::host;
 
 namespace {
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 512;
 constexpr long long kBatchWarps = kBatchThreads / 32;
 
 enum : int { kModeScale = 1, kModeRefresh = 2, kModeReset = 4 };
@@ -36,7 +36,7 @@ enum : int { kModeScale = 1, kModeRefresh = 2, kModeReset = 4 };
 constexpr int kModeShift = 28;
 
 template <typename T>
-__global__ void __launch_bounds__(kBatchThreads, 2)
+__global__ void __launch_bounds__(kBatchThreads, 1)
     k_batch(const Dev<T>* __restrict__ devs, const int* __restrict__ order, int count,
             const __grid_constant__ Params P, int* queue, unsigned long long* times) {
   __shared__ double sm[kSmemDoubles];
@@ -183,6 +183,8 @@ struct osqp_batch {
   std::vector<int> order;           // problems sorted by work, largest first
   std::vector<int> mode;            // per-problem kernel mode for the next launch
   std::vector<unsigned long long> times_host;
+  std::vector<double> last_dur;     // device seconds of problem i in its last launch (0: none)
+  bool unrecorded = false;          // a whole-batch launch whose times are not in last_dur
   char* arena = nullptr;
   size_t static_bytes = 0, arena_bytes = 0;
   void* devs = nullptr;             // Dev<T>[count]
@@ -279,11 +281,51 @@ int batch_launch(osqp_batch* b, const std::vector<int>& sel) {
   return OSQP_OK;
 }
 
-int batch_wait(osqp_batch* b) {
+// Per-problem device times of the launch that just completed → last_dur.
+void record_durations(osqp_batch* b, const std::vector<int>& sel) {
+  if (sel.empty()) return;
+  if (cudaMemcpy(b->times_host.data(), b->times_d, sizeof(unsigned long long) * b->times_host.size(),
+                 cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  for (int v : sel) {
+    const unsigned long long t0 = b->times_host[2 * (size_t)v], t1 = b->times_host[2 * (size_t)v + 1];
+    if (t1 > t0) b->last_dur[v] = (double)(t1 - t0) * 1e-9;
+  }
+}
+
+// Launch order, longest first (a longest-processing-time schedule of the
+// problems over the persistent CTAs).  The key is each problem's device time
+// in its last launch when every selected problem has one — a batch that is
+// solved again and again (parametric MPC, serving) knows its slow problems,
+// which depend on iteration counts more than on size — else the static work
+// estimate.  The order changes only which CTA solves a problem, never a result.
+void order_longest_first(const osqp_batch* b, std::vector<int>& sel) {
+  bool hist = true;
+  for (int v : sel)
+    if (!(b->last_dur[v] > 0.0)) {
+      hist = false;
+      break;
+    }
+  if (hist) {
+    std::stable_sort(sel.begin(), sel.end(),
+                     [&](int a, int c) { return b->last_dur[a] > b->last_dur[c]; });
+  } else {
+    std::stable_sort(sel.begin(), sel.end(), [&](int a, int c) {
+      return (long long)b->L[a].nnz_kn + b->L[a].nnz_a + b->L[a].n + b->L[a].m >
+             (long long)b->L[c].nnz_kn + b->L[c].nnz_a + b->L[c].n + b->L[c].m;
+    });
+  }
+}
+
+int batch_wait(osqp_batch* b, const std::vector<int>& sel) {
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
   float ms = 0.f;
   if (b->solved && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess)
     b->last_time = ms * 1e-3;
+  record_durations(b, sel);
+  b->unrecorded = false;
   return OSQP_OK;
 }
 
@@ -466,16 +508,11 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
   }
   b->mode.assign(count, kModeScale);
   b->times_host.assign(2 * (size_t)count, 0);
-  // Work order: largest problem first (a longest-processing-time schedule).
+  b->last_dur.assign(count, 0.0);
+  if (cudaMemset(b->times_d, 0, sizeof(unsigned long long) * 2 * count) != cudaSuccess)
+    return fail(OSQP_ERR_CUDA);
   b->order.resize(count);
   std::iota(b->order.begin(), b->order.end(), 0);
-  std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) {
-    return (long long)b->L[a].nnz_kn + b->L[a].nnz_a + b->L[a].n + b->L[a].m >
-           (long long)b->L[c].nnz_kn + b->L[c].nnz_a + b->L[c].n + b->L[c].m;
-  });
-  if (cudaMemcpy(b->order_d, b->order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) !=
-      cudaSuccess)
-    return fail(OSQP_ERR_CUDA);
   *out = b;
   return OSQP_OK;
 }
@@ -486,13 +523,22 @@ int32_t osqp_batch_solve_async(osqp_batch* b) {
     if (v >= 0) return OSQP_ERR_ARG;  // a slot launch is still in flight
   if (!b->set.warm_start)
     for (int i = 0; i < b->count; ++i) b->mode[i] |= kModeReset;
-  return batch_launch(b, b->order);
+  // times of an earlier asynchronous launch, if it has finished (no wait)
+  if (b->unrecorded && cudaStreamQuery(b->stream) == cudaSuccess) {
+    record_durations(b, b->order);
+    b->unrecorded = false;
+  }
+  cudaGetLastError();
+  order_longest_first(b, b->order);
+  const int rc = batch_launch(b, b->order);
+  if (rc == OSQP_OK) b->unrecorded = true;
+  return rc;
 }
 
 int32_t osqp_batch_solve(osqp_batch* b) {
   const int rc = osqp_batch_solve_async(b);
   if (rc) return rc;
-  return batch_wait(b);
+  return batch_wait(b, b->order);
 }
 
 int32_t osqp_batch_solve_subset(osqp_batch* b, const int32_t* idx, int32_t k) {
@@ -501,14 +547,12 @@ int32_t osqp_batch_solve_subset(osqp_batch* b, const int32_t* idx, int32_t k) {
   std::vector<int> sel(idx, idx + k);
   for (int v : sel)
     if (v < 0 || v >= b->count || b->inflight[v] >= 0) return OSQP_ERR_ARG;
-  std::stable_sort(sel.begin(), sel.end(), [&](int a, int c) {
-    return (long long)b->L[a].nnz_kn + b->L[a].nnz_a > (long long)b->L[c].nnz_kn + b->L[c].nnz_a;
-  });
+  order_longest_first(b, sel);
   if (!b->set.warm_start)
     for (int v : sel) b->mode[v] |= kModeReset;
   const int rc = batch_launch(b, sel);
   if (rc) return rc;
-  return batch_wait(b);
+  return batch_wait(b, sel);
 }
 
 int32_t osqp_batch_reset(osqp_batch* b) {
@@ -587,9 +631,7 @@ int32_t osqp_batch_launch(osqp_batch* b, int32_t slot, const int32_t* idx, int32
   }
   if (!b->set.warm_start)
     for (int v : sel) b->mode[v] |= kModeReset;
-  std::stable_sort(sel.begin(), sel.end(), [&](int a, int c) {
-    return (long long)b->L[a].nnz_kn + b->L[a].nnz_a > (long long)b->L[c].nnz_kn + b->L[c].nnz_a;
-  });
+  order_longest_first(b, sel);
   const int rc = b->set.precision == OSQP_PRECISION_FP64
                      ? launch_batch<double>(b, sel, S.order, S.queue, S.stream)
                      : launch_batch<float>(b, sel, S.order, S.queue, S.stream);
@@ -602,7 +644,13 @@ int32_t osqp_batch_launch(osqp_batch* b, int32_t slot, const int32_t* idx, int32
 
 static void retire(osqp_batch* b, int slot) {
   osqp_batch::Slot& S = b->slots[slot];
-  for (int v : S.members) b->inflight[v] = -1;
+  for (int v : S.members) {
+    b->inflight[v] = -1;
+    unsigned long long t[2];
+    if (cudaMemcpy(t, b->times_d + 2 * (size_t)v, sizeof(t), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        t[1] > t[0])
+      b->last_dur[v] = (double)(t[1] - t[0]) * 1e-9;
+  }
   S.members.clear();
 }
 
