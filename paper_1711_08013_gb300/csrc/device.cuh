@@ -204,6 +204,71 @@ __device__ __forceinline__ void block_reduce(const double (&v)[K], double* sm) {
   __syncthreads();
 }
 
+// Order-preserving 32-bit key of a float (NaN above +∞).
+__device__ __forceinline__ unsigned fkey(float v) {
+  const unsigned b = __float_as_uint(v);
+  return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float funkey(unsigned k) {
+  return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Block-wide reduction of K working-precision (FP32) slots with the result
+// in FP64, for the FP32-mixed mode: each warp sums its lanes' values by a
+// shuffle tree of error-free FP32 additions (Knuth's TwoSum, the rounding
+// errors carried in a second FP32 term), so the narrow FP64 pipe only adds
+// one value per warp.  Max slots combine order-preserving keys.  Result in
+// sm[32*kMaxRed + k], as block_reduce.  All threads call it.
+template <int K, unsigned MAXMASK>
+__device__ __forceinline__ void block_reduce(const float (&v)[K], double* sm) {
+  static_assert(K <= kMaxSumSlots, "too many slots");
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double w;
+    if ((MAXMASK >> k) & 1u) {
+      unsigned x = fkey(v[k]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned o = __shfl_xor_sync(0xffffffffu, x, off);
+        x = x > o ? x : o;
+      }
+      w = (double)funkey(x);
+    } else {
+      float hi = v[k], lo = 0.0f;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float b = __shfl_xor_sync(0xffffffffu, hi, off);
+        const float bl = __shfl_xor_sync(0xffffffffu, lo, off);
+        const float s = __fadd_rn(hi, b);
+        const float bb = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(bl, err));
+      }
+      w = (double)hi + (double)lo;
+    }
+    if (lane == 0) sm[wid * kMaxRed + k] = w;
+  }
+  __syncthreads();
+  if (wid < K) {
+    const int k = wid;
+    const bool mx = (MAXMASK >> k) & 1u;
+    if (mx) {
+      unsigned long long x = lane < nw ? dkey(sm[lane * kMaxRed + k]) : 0ull;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x = umax64(x, __shfl_xor_sync(0xffffffffu, x, off));
+      if (lane == 0) sm[32 * kMaxRed + k] = dunkey(x);
+    } else {
+      double x = lane < nw ? sm[lane * kMaxRed + k] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      if (lane == 0) sm[32 * kMaxRed + k] = x;
+    }
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Teams
 // ---------------------------------------------------------------------------
@@ -224,38 +289,43 @@ struct GridTeam {
 
   // Grid barrier with a bounded wait.  The arrival counter only grows
   // during a launch (the host zeroes it before every launch), so barrier
-  // number k is complete once it reaches k·gridDim.x.  A CTA that waits
-  // longer than timeout_ns records kDevBarrierTimeout and leaves; every CTA
-  // stops at its next barrier.
+  // number k is complete once it reaches k·gridDim.x.  Thread 0 arrives with
+  // an acquire-release atomic and spins with acquire loads, so the CTA's
+  // writes before the barrier are visible to every CTA after it.  A CTA that
+  // waits longer than timeout_ns records kDevBarrierTimeout and adds
+  // kBarrierPoison to the counter, which releases every waiter at once; a
+  // counter at or above kBarrierPoison makes every CTA stop at its barrier.
+  static constexpr unsigned int kBarrierPoison = 0x80000000u;
   __device__ bool sync() {
     __syncthreads();
+    int* flag = reinterpret_cast<int*>(sm + 34 * kMaxRed - 1);
     if (threadIdx.x == 0) {
       target += gridDim.x;
-      __threadfence();
-      atomicAdd(&bar->count, 1u);
-      volatile unsigned int* vcount = &bar->count;
-      int ok = 1;
-      if (*vcount < target) {
+      unsigned int c;
+      asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(c) : "l"(&bar->count) : "memory");
+      c += 1u;
+      if (c < target) {
         const unsigned long long t0 = gtimer();
         unsigned int spins = 0;
-        while (*vcount < target) {
+        for (;;) {
+          asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(c) : "l"(&bar->count) : "memory");
+          if (c >= target) break;
           if ((++spins & 255u) == 0 && gtimer() - t0 > timeout_ns) {
             atomicExch(err, kDevBarrierTimeout);
-            ok = 0;
+            atomicAdd(&bar->count, kBarrierPoison);
+            c = kBarrierPoison;
             break;
           }
         }
       }
-      __threadfence();
-      if (ok && *(volatile int*)err != kDevOk) ok = 0;
-      sm[34 * kMaxRed - 1] = ok ? 1.0 : 0.0;
+      *flag = c < kBarrierPoison ? 1 : 0;
     }
     __syncthreads();
-    return sm[34 * kMaxRed - 1] != 0.0;
+    return *flag != 0;
   }
 
-  template <int K, unsigned MAXMASK>
-  __device__ void publish(const double (&v)[K]) {
+  template <int K, unsigned MAXMASK, typename V>
+  __device__ void publish(const V (&v)[K]) {
     block_reduce<K, MAXMASK>(v, sm);
     if (threadIdx.x < K)
       part[((size_t)buf * gridDim.x + blockIdx.x) * kMaxRed + threadIdx.x] =
@@ -272,25 +342,28 @@ struct GridTeam {
     for (int k = wid; k < K; k += nw) {
       const bool mx = (MAXMASK >> k) & 1u;
       const double* src = part + (size_t)buf * nb * kMaxRed + k;
+      // the ⌈nb/32⌉ partials of a lane, loaded together, then combined in
+      // lane order (no FP64 work on absent partials)
+      const int per = (nb + 31) >> 5;
       double y[16];
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int b = lane + 32 * u;
-        y[u] = b < nb ? __ldcg(src + (size_t)b * kMaxRed) : (mx ? -INFINITY : 0.0);
+        y[u] = (u < per && b < nb) ? __ldcg(src + (size_t)b * kMaxRed) : (mx ? -INFINITY : 0.0);
       }
       if (mx) {
         unsigned long long x = dkey(y[0]);
 #pragma unroll
-        for (int u = 1; u < 16; ++u) x = umax64(x, dkey(y[u]));
+        for (int u = 1; u < 16; ++u)
+          if (u < per) x = umax64(x, dkey(y[u]));
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x = umax64(x, __shfl_xor_sync(0xffffffffu, x, off));
         if (lane == 0) sm[33 * kMaxRed + k] = dunkey(x);
       } else {
-#pragma unroll
-        for (int w = 8; w > 0; w >>= 1)
-#pragma unroll
-          for (int u = 0; u < w; ++u) y[u] += y[u + w];
         double x = y[0];
+#pragma unroll
+        for (int u = 1; u < 16; ++u)
+          if (u < per) x += y[u];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
         if (lane == 0) sm[33 * kMaxRed + k] = x;
@@ -314,8 +387,8 @@ struct BlockTeam {
     __syncthreads();
     return true;
   }
-  template <int K, unsigned MAXMASK>
-  __device__ void publish(const double (&v)[K]) {
+  template <int K, unsigned MAXMASK, typename V>
+  __device__ void publish(const V (&v)[K]) {
     block_reduce<K, MAXMASK>(v, sm);
   }
   template <int K, unsigned MAXMASK>
@@ -762,7 +835,8 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     // w = Ku and the two inner products (r,u), (w,u).  r, s, w and t are
     // double-buffered so that gathers never see a vector being rewritten.
     // --- A0: u = M⁻¹r, t = RĀu; (r,u), ‖r‖∞, ‖b‖∞
-    double red3[3] = {0.0, 0.0, 0.0};
+    double red3[3];
+    T red3t[3];
     {
       const T* __restrict__ r = rbuf(cur);
       T* __restrict__ t = tbuf(cur);
@@ -775,9 +849,9 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         a1 = fmax(a1, fabs(rj));
         a2 = fmax(a2, fabs(bv[j]));
       }
-      red3[0] = (double)a0;
-      red3[1] = (double)a1;
-      red3[2] = (double)a2;
+      red3t[0] = a0;
+      red3t[1] = a1;
+      red3t[2] = a2;
       spmv<1, false, T, T>(
           tm, d.as, a_ci, a_v,
           [&](int col, T v, T* acc) { acc[0] += v * (r[col] * dinv[col]); },
@@ -785,7 +859,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           [&](int i, int, T* acc) { atomicAdd(&t[i], rhoT[i] * acc[0]); });
       zero_long(tm, d.kn, wbuf(cur));
     }
-    tm.template publish<3, 6u>(red3);
+    tm.template publish<3, 6u>(red3t);
     if (!tm.sync()) return false;
     tm.template collect<3, 6u>(red3);
     double gamma = red3[0];
@@ -814,8 +888,8 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
             atomicAdd(&w[j], part);
             wacc += part * u[j];
           });
-      red1[0] = (double)wacc;
-      tm.template publish<1, 0u>(red1);
+      const T red1t[1] = {wacc};
+      tm.template publish<1, 0u>(red1t);
       if (!tm.sync()) return false;
       tm.template collect<1, 0u>(red1);
       if (red1[0] > 0.0) alpha_c = gamma / red1[0];
@@ -866,7 +940,8 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       ++j_it;
       ++pcg_total;
       // --- P2: w = Ku, (r,u), (w,u), ‖r‖∞
-      double red2[3] = {0.0, 0.0, 0.0};
+      double red2[3];
+      T red2t[3];
       {
         const T* __restrict__ rn = rbuf(nxt);
         T* __restrict__ wn = wbuf(nxt);
@@ -891,11 +966,11 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
               g1 += part * u[j];
             });
         zero_long(tm, d.as, tbuf(cur));
-        red2[0] = (double)g0;
-        red2[1] = (double)g1;
-        red2[2] = (double)g2;
+        red2t[0] = g0;
+        red2t[1] = g1;
+        red2t[2] = g2;
       }
-      tm.template publish<3, 4u>(red2);
+      tm.template publish<3, 4u>(red2t);
       if (!tm.sync()) return false;
       tm.template collect<3, 4u>(red2);
       cur = nxt;
