@@ -59,6 +59,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     } else {
       if (md & kModeRefresh) refresh_stage(tm, d, P, rho_bar);
       if (md & kModeReset) {
+        if (threadIdx.x == 0) {
+          d.sc->rp_last = 0.0;
+          d.sc->rd_last = 0.0;
+        }
         for (int j = threadIdx.x; j < d.n; j += blockDim.x) {
           d.x[j] = 0.0;
           d.dx[j] = 0.0;

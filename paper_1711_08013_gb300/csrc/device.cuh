@@ -65,6 +65,10 @@ struct Scalars {
   double obj, prim_res, dual_res;
   int status, iter, pcg_iters, rho_updates, ruiz_passes, checks;
   int dev_error, pad;
+  // scaled primal/dual residuals of the last termination check; a solve that
+  // continues from the current iterates takes its first PCG tolerance from
+  // them (0: no check since the iterates were last reset)
+  double rp_last, rd_last;
 };
 
 struct Params {
@@ -680,6 +684,10 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
   if (!tm.sync()) return false;
   jacobi_rows(tm, d, P.sigma, rho_bar);
   if (reset_iterates) {
+    if (tm.leader()) {
+      d.sc->rp_last = 0.0;
+      d.sc->rd_last = 0.0;
+    }
     for (int j = tid; j < n; j += nth) {
       d.x[j] = 0.0;
       d.dx[j] = 0.0;
@@ -775,8 +783,12 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   const double* __restrict__ rho_inv = d.rho_inv;
 
   int status = kUnsolved, k = 0, pcg_total = 0, rho_updates = 0, checks = 0;
-  bool dinv_dirty = false, have_check = false;
-  double rp_bar = 0.0, rd_bar = 0.0, prim_res = NAN, dual_res = NAN, obj = NAN;
+  bool dinv_dirty = false;
+  // PCG tolerance before this solve's first check: the residuals of the last
+  // check on the current iterates (a warm start), else a fraction of ‖b‖
+  double rp_bar = d.sc->rp_last, rd_bar = d.sc->rd_last;
+  bool have_check = rp_bar > 0.0 && rd_bar > 0.0;
+  double prim_res = NAN, dual_res = NAN, obj = NAN;
   int cur = 0;
 
   // Right-hand-side inputs of the first iteration from the current iterates.
@@ -1147,6 +1159,10 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       status = kDualInf;
     } else if (P.time_limit_ns > 0.0 && R[23] > P.time_limit_ns) {
       status = kTimeLimit;
+    }
+    if (tm.leader()) {
+      d.sc->rp_last = R[3];
+      d.sc->rd_last = R[10];
     }
     if (status != kUnsolved) break;
     rp_bar = R[3];

@@ -95,6 +95,10 @@ __global__ void k_warm_xy(const __grid_constant__ Dev<T> d, const double* __rest
                           const double* __restrict__ yw) {
   const double c = d.sc->c;
   const int stride = gridDim.x * blockDim.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // new iterates: no check on them yet
+    d.sc->rp_last = 0.0;
+    d.sc->rd_last = 0.0;
+  }
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
     const double xv = xw ? xw[j] / d.D[j] : 0.0;
     d.x[j] = xv;
@@ -128,6 +132,10 @@ __global__ void k_warm_z(const __grid_constant__ Dev<T> d) {
 template <typename T>
 __global__ void k_zero_iterates(const __grid_constant__ Dev<T> d) {
   const int stride = gridDim.x * blockDim.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d.sc->rp_last = 0.0;
+    d.sc->rd_last = 0.0;
+  }
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
     d.x[j] = 0.0;
     d.dx[j] = 0.0;

@@ -134,14 +134,18 @@ def eq_qp(n: int, seed: int = 0, density: float = 0.15) -> QP:
 # App. A.3: optimal control (MPC), with the ranges of the batched workload
 # ----------------------------------------------------------------------------
 def mpc(nx: int, T: int, seed: int = 0, nu: int | None = None, q_density: float = 0.10,
-        xbar_range=(1.0, 2.0), ubar_range=(0.5, 1.5), x0_range=(-0.5, 0.5)) -> QP:
+        xbar_range=(1.0, 2.0), ubar_range=(0.5, 1.5), x0_range=(-0.5, 0.5),
+        x0_scale: float | None = None, terminal: str = "Q") -> QP:
     """App. A.3 MPC QP in z = (x_0..x_T, u_0..u_{T-1}).
 
     Dynamics A_d = I + 0.1·N(0,1), scaled by 0.99/ρ(A_d) when its spectral
     radius exceeds 0.99; B_d ~ N(0,1); Q = diag(q) with q at `q_density`
-    U[0,10]; R = 0.1·I; terminal cost Q_T = Q; |x_t| ≤ x̄, |u_t| ≤ ū;
-    x_0 = x_init.  Rows: x_0 = x_init, A_d x_t + B_d u_t − x_{t+1} = 0
-    (equalities), then the state and input boxes.
+    U[0,10]; R = 0.1·I; terminal cost Q_T = Q, or with terminal="dare" the
+    LQR cost-to-go of (A_d, B_d, Q, R) from the discrete algebraic Riccati
+    equation; |x_t| ≤ x̄, |u_t| ≤ ū; x_0 = x_init with x_init ~ U(x0_range),
+    or U(−s·x̄, s·x̄) for x0_scale = s.  Rows: x_0 = x_init, A_d x_t + B_d u_t
+    − x_{t+1} = 0 (equalities), then the state and input boxes.  meta keeps
+    A_d, B_d, x̄, ū and x_init for closed-loop simulation.
     """
     rng = np.random.default_rng(seed)
     nu = nx // 2 if nu is None else nu
@@ -153,13 +157,25 @@ def mpc(nx: int, T: int, seed: int = 0, nu: int | None = None, q_density: float 
     qd = np.where(rng.random(nx) < q_density, 10.0 * rng.random(nx), 0.0)
     xbar = rng.uniform(*xbar_range, size=nx)
     ubar = rng.uniform(*ubar_range, size=nu)
-    x0 = rng.uniform(*x0_range, size=nx)
+    if x0_scale is None:
+        x0 = rng.uniform(*x0_range, size=nx)
+    else:
+        x0 = rng.uniform(-1.0, 1.0, size=nx) * x0_scale * xbar
 
     nX = nx * (T + 1)
     n = nX + nu * T
     # P = 2·blockdiag(Q, …, Q, Q_T, R, …, R), objective read without the ½.
-    pdiag = np.concatenate([np.tile(qd, T + 1), np.full(nu * T, 0.1)]) * 2.0
-    P = sp.diags(pdiag, format="csc")
+    if terminal == "Q":
+        pdiag = np.concatenate([np.tile(qd, T + 1), np.full(nu * T, 0.1)]) * 2.0
+        P = sp.diags(pdiag, format="csc")
+    elif terminal == "dare":
+        import scipy.linalg as sla
+        QT = sla.solve_discrete_are(Ad, Bd, np.diag(qd), 0.1 * np.eye(nu))
+        QT = 0.5 * (QT + QT.T)
+        P = 2.0 * sp.block_diag([sp.diags(np.tile(qd, T)), sp.csc_matrix(QT),
+                                 sp.diags(np.full(nu * T, 0.1))], format="csc")
+    else:
+        raise ValueError("terminal must be 'Q' or 'dare'")
     q = np.zeros(n)
 
     # Equality block: rows 0..nx-1: x_0 = x0; rows nx(t+1)..: A_d x_t + B_d u_t - x_{t+1} = 0
@@ -176,7 +192,15 @@ def mpc(nx: int, T: int, seed: int = 0, nu: int | None = None, q_density: float 
     l = np.concatenate([beq, lbox])
     u = np.concatenate([beq, ubox])
     return _finish(f"mpc_nx{nx}_T{T}_s{seed}", P, q, A, l, u, cls="mpc", nx=nx, nu=nu, T=T,
-                   seed=seed)
+                   seed=seed, Ad=Ad, Bd=Bd, xbar=xbar, ubar=ubar, x0=x0)
+
+
+def mpc_paper(nx: int, T: int = 10, seed: int = 0) -> QP:
+    """App. A.3 with the paper's own instance ranges (the parametric
+    closed-loop workload of §8.4): q at 70% density, ū ~ U(0, 0.1),
+    x_init ~ U(−0.5x̄, 0.5x̄), Q_T from the Riccati equation."""
+    return mpc(nx, T, seed=seed, q_density=0.7, ubar_range=(0.0, 0.1), x0_scale=0.5,
+               terminal="dare")
 
 
 def mpc_batch(count: int = 4096, seed: int = 3000, nx_range=(4, 32), T_range=(10, 30)) -> list[QP]:
@@ -191,15 +215,10 @@ def mpc_batch(count: int = 4096, seed: int = 3000, nx_range=(4, 32), T_range=(10
 # ----------------------------------------------------------------------------
 # App. A.4: portfolio optimisation (factor model)
 # ----------------------------------------------------------------------------
-def portfolio(k: int, seed: int = 0, n: int | None = None, gamma: float = 1.0) -> QP:
-    """App. A.4 in variables (x, y), y = Fᵀx: P = blockdiag(2D, 2I),
-    q = (−μ/γ, 0); rows Fᵀx − y = 0, 1ᵀx = 1, x ≥ 0.  n = 100k assets,
-    F at 50% N(0,1), D_ii ~ U[0, √k], μ ~ N(0,1)."""
-    rng = np.random.default_rng(seed)
-    n = 100 * k if n is None else n
-    F = sprandn(rng, n, k, 0.5)
-    Dd = rng.uniform(0.0, math.sqrt(k), size=n)
-    mu = rng.standard_normal(n)
+def portfolio_data(F: sp.csc_matrix, Dd: np.ndarray, mu: np.ndarray, gamma: float = 1.0):
+    """(P, q, A, l, u) of App. A.4 in variables (x, y), y = Fᵀx: P =
+    blockdiag(2D, 2I), q = (−μ/γ, 0); rows Fᵀx − y = 0, 1ᵀx = 1, x ≥ 0."""
+    n, k = F.shape
     P = sp.diags(np.concatenate([2.0 * Dd, 2.0 * np.ones(k)]), format="csc")
     q = np.concatenate([-mu / gamma, np.zeros(k)])
     A = sp.vstack([
@@ -209,8 +228,21 @@ def portfolio(k: int, seed: int = 0, n: int | None = None, gamma: float = 1.0) -
     ]).tocsc()
     l = np.concatenate([np.zeros(k), [1.0], np.zeros(n)])
     u = np.concatenate([np.zeros(k), [1.0], np.full(n, np.inf)])
+    return P, q, A, l, u
+
+
+def portfolio(k: int, seed: int = 0, n: int | None = None, gamma: float = 1.0) -> QP:
+    """App. A.4 in variables (x, y), y = Fᵀx (see portfolio_data); n = 100k
+    assets, F at 50% N(0,1), D_ii ~ U[0, √k], μ ~ N(0,1).  meta keeps F, D
+    and μ for the back test of §8.4."""
+    rng = np.random.default_rng(seed)
+    n = 100 * k if n is None else n
+    F = sprandn(rng, n, k, 0.5)
+    Dd = rng.uniform(0.0, math.sqrt(k), size=n)
+    mu = rng.standard_normal(n)
+    P, q, A, l, u = portfolio_data(F, Dd, mu, gamma)
     return _finish(f"portfolio_k{k}_n{n}_s{seed}", P, q, A, l, u, cls="portfolio", k=k,
-                   seed=seed)
+                   seed=seed, F=F, D=Dd, mu=mu, gamma=gamma)
 
 
 # ----------------------------------------------------------------------------
@@ -237,7 +269,7 @@ def lasso(n: int, seed: int = 0, m: int | None = None, lam_frac: float = 0.2) ->
     l = np.concatenate([b, np.full(n, -np.inf), np.zeros(n)])
     u = np.concatenate([b, np.zeros(n), np.full(n, np.inf)])
     return _finish(f"lasso_n{n}_m{m}_s{seed}", P, q, A, l, u, cls="lasso", lam=lam,
-                   n_feat=n, m_data=m, seed=seed)
+                   lam_max=lam / lam_frac, n_feat=n, m_data=m, seed=seed)
 
 
 # ----------------------------------------------------------------------------
