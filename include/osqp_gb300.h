@@ -98,7 +98,9 @@ typedef struct {
   int32_t warm_start;            /* 1: osqp_solve starts from the current iterates
                                     (§6); 0: from zero.  Default 1 */
   int32_t launch;                /* 0 auto, 1 one persistent block, 2 whole-GPU
-                                    cooperative grid */
+                                    cooperative grid, 3 one thread-block cluster
+                                    of 8 CTAs (OSQP_ERR_CUDA at setup if the
+                                    device cannot host such a cluster) */
 } osqp_settings;
 
 typedef struct {
@@ -188,12 +190,22 @@ int32_t osqp_cleanup(osqp_solver* s);
  * first) and runs the complete solve of the single-problem entry points for
  * them (Alg. 2 scaling, Algorithm 1 with PCG, §3.4/§5.1 termination, §5.2 ρ̄
  * adaptation).  Problems share no reduction, so a problem's result does not
- * depend on which other problems are in the batch. */
+ * depend on which other problems are in the batch (it may depend, at the
+ * rounding level, on whether one CTA or a cluster solved it; see below).
+ *
+ * Work order is longest first: by each problem's device time in its previous
+ * launch when every problem of the launch has one, else by size.  In a
+ * whole-batch launch with more problems than CTAs and known times, the
+ * problems whose time exceeds the fair share (total / CTAs) are solved
+ * by clusters of 8 CTAs on a second stream beside the one-CTA kernel (they
+ * would otherwise set the wall time); osqp_batch_get reports launch = 3 for
+ * them.  settings->launch = 1 keeps every problem on one CTA. */
 typedef struct osqp_batch osqp_batch;
 
 /* count problems; P_upper[i], A[i] (host CSC as for osqp_setup) and
  * q[i], l[i], u[i] (host arrays).  One device allocation holds everything.
- * The settings apply to every problem; settings->launch is ignored. */
+ * The settings apply to every problem; settings->launch other than 1 only
+ * allows the heavy-problem clusters described above. */
 int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P_upper,
                          const double* const* q, const osqp_csc* A, const double* const* l,
                          const double* const* u, const osqp_settings* settings, void* stream);
@@ -253,6 +265,16 @@ int32_t osqp_batch_slot_wait(osqp_batch* b, int32_t slot);
 int64_t osqp_batch_footprint(const osqp_batch* b, int32_t i);
 
 int32_t osqp_batch_cleanup(osqp_batch* b);
+
+/* Diagnostic of the bounded grid barrier that every multi-CTA solve relies
+ * on (the paper has no counterpart).  Launches four cooperative CTAs on the
+ * current device, one of which never arrives at the barrier; the others must
+ * give up after timeout_s seconds (0 < timeout_s ≤ 10), record the timeout
+ * and return, leaving the context usable.  Returns OSQP_OK when exactly
+ * that happened, OSQP_ERR_DEVICE if the barrier did not report the timeout,
+ * OSQP_ERR_ARG for a bad timeout, OSQP_ERR_CUDA on a CUDA error.  Allocates
+ * and frees a few bytes of device memory; synchronises the device. */
+int32_t osqp_diag_barrier_timeout(double timeout_s);
 
 #ifdef __cplusplus
 }

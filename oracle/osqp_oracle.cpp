@@ -103,8 +103,11 @@ Csc full_from_upper(int n, const int* Pp, const int* Pi, const double* Px) {
 // Modified Ruiz equilibration, Alg. 2 (§5.1), on M = [P Aᵀ; A 0] (Eq. equil_matrix).
 // Readings: at most `iters` passes, stopping early once ‖1 − δ‖∞ ≤ ε_equil;
 // a norm of exactly 0 gives δ = 1, other norms are clamped to [1e-4, 1e4];
-// γ uses the mean over all n columns of P̄ and is left at 1 when
-// max(mean, ‖q̄‖∞) < 1e-4.
+// γ uses the mean over all n columns of P̄; in γ's max a norm below 1e-4
+// counts as 1 (a vanishing norm carries no scale, as for δ), and the max is
+// clamped to [1e-4, 1e4].  (Taken literally with q̄ = 0 and mostly-zero P̄
+// columns, 1/max grows c geometrically pass after pass, which inflates the
+// cost and the duals that the step exists to normalise.)
 // ---------------------------------------------------------------------------
 struct Scaling {
   std::vector<double> D, E;
@@ -153,8 +156,10 @@ Scaling ruiz(Csc& P, std::vector<double>& q, Csc& A, std::vector<double>& l,
     }
     mean /= std::max(n, 1);
     double qn = inf_norm(q);
-    double mx = std::max(mean, qn);
-    double gamma = mx < kNormMin ? 1.0 : 1.0 / mx;
+    if (mean < kNormMin) mean = 1.0;
+    if (qn < kNormMin) qn = 1.0;
+    const double mx = std::min(std::max(std::max(mean, qn), kNormMin), kNormMax);
+    const double gamma = 1.0 / mx;
     for (double& v : P.x) v *= gamma;
     for (double& v : q) v *= gamma;
     // S ← diag(δ)S, c ← γc

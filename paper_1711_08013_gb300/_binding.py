@@ -75,6 +75,7 @@ _SIGS = {
     "osqp_get_solution_device": (C.c_int32, [_P, _P, _P]),
     "osqp_get_certificate": (C.c_int32, [_P, _P, _P]),
     "osqp_cleanup": (C.c_int32, [_P]),
+    "osqp_diag_barrier_timeout": (C.c_int32, [C.c_double]),
     "osqp_batch_setup": (C.c_int32, [C.POINTER(_P), C.c_int32, _P, _P, _P, _P, _P,
                                      C.POINTER(osqp_settings), _P]),
     "osqp_batch_solve": (C.c_int32, [_P]),

@@ -27,6 +27,9 @@ namespace {
 
 constexpr int kBatchThreads = 512;
 constexpr long long kBatchWarps = kBatchThreads / 32;
+constexpr int kBatchCluster = 8;      // CTAs of a heavy-problem cluster
+constexpr int kMaxHeavyClusters = 4;  // clusters a launch may take for heavy problems
+constexpr int kMaxHeavy = 32;         // heavy problems per launch at most
 
 enum : int { kModeScale = 1, kModeRefresh = 2, kModeReset = 4 };
 
@@ -34,6 +37,37 @@ enum : int { kModeScale = 1, kModeRefresh = 2, kModeReset = 4 };
 // problem travel with the launch that solves it, so concurrent launches on
 // different streams never share mutable per-problem flags.
 constexpr int kModeShift = 28;
+
+// One problem of a batch launch on a team: the mode bits of its queue entry
+// (first scaling, data refresh, iterate reset), then Algorithm 1.
+template <class Team, typename T>
+__device__ void batch_solve_one(Team& tm, const Dev<T>& d, const Params& P, int md) {
+  const double rho_bar = d.sc->rho_bar;
+  if (md & kModeScale) {
+    if (!scale_stage(tm, d, P, rho_bar, true)) return;
+  } else {
+    if ((md & kModeRefresh) && !refresh_stage(tm, d, P, rho_bar)) return;
+    if (md & kModeReset) {
+      if (tm.leader()) {
+        d.sc->rp_last = 0.0;
+        d.sc->rd_last = 0.0;
+      }
+      for (int j = tm.tid(); j < d.n; j += tm.nthreads()) {
+        d.x[j] = 0.0;
+        d.dx[j] = 0.0;
+        d.xt[j] = 0.0;
+      }
+      for (int i = tm.tid(); i < d.m; i += tm.nthreads()) {
+        d.z[i] = 0.0;
+        d.y[i] = 0.0;
+        d.dy[i] = 0.0;
+        d.zt[i] = 0.0;
+      }
+      if (!tm.sync()) return;
+    }
+  }
+  admm_stage(tm, d, P);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kBatchThreads, 1)
@@ -50,40 +84,69 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     if (idx >= count) break;
     const int code = order[idx];
     const int p = code & ((1 << kModeShift) - 1);
-    const int md = code >> kModeShift;
     const Dev<T>& d = devs[p];
     const unsigned long long t0 = gtimer();
-    const double rho_bar = d.sc->rho_bar;
-    if (md & kModeScale) {
-      scale_stage(tm, d, P, rho_bar, true);
-    } else {
-      if (md & kModeRefresh) refresh_stage(tm, d, P, rho_bar);
-      if (md & kModeReset) {
-        if (threadIdx.x == 0) {
-          d.sc->rp_last = 0.0;
-          d.sc->rd_last = 0.0;
-        }
-        for (int j = threadIdx.x; j < d.n; j += blockDim.x) {
-          d.x[j] = 0.0;
-          d.dx[j] = 0.0;
-          d.xt[j] = 0.0;
-        }
-        for (int i = threadIdx.x; i < d.m; i += blockDim.x) {
-          d.z[i] = 0.0;
-          d.y[i] = 0.0;
-          d.dy[i] = 0.0;
-          d.zt[i] = 0.0;
-        }
-        __syncthreads();
-      }
-    }
-    admm_stage(tm, d, P);
+    batch_solve_one(tm, d, P, code >> kModeShift);
     __syncthreads();
     if (threadIdx.x == 0) {
       times[2 * p] = t0;
       times[2 * p + 1] = gtimer();
     }
   }
+}
+
+// Clusters of kBatchCluster CTAs for the heaviest problems of a launch:
+// each cluster takes problems from the heavy queue, then joins the queue of
+// the one-CTA kernel running beside it (shared counter), so no SM idles
+// once the heavy problems are done.  Rank 0 takes the index and the others
+// read it through distributed shared memory; every decision is taken on
+// values identical in all CTAs, so all CTAs leave the loop together.
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads, 1)
+    k_batch_cluster(const Dev<T>* __restrict__ devs, const int* __restrict__ order_h, int count_h,
+                    int* queue_h, const int* __restrict__ order_l, int count_l, int* queue_l,
+                    const __grid_constant__ Params P, unsigned long long* times, int* err) {
+  __shared__ double sm[kSmemDoubles];
+  __shared__ double cpart[2 * kMaxRed];
+  __shared__ unsigned ctr;
+  __shared__ int sidx;
+  if (threadIdx.x == 0) ctr = 0u;
+  cluster_sync_all();
+  ClusterTeam tm{sm, cpart, &ctr, err, P.barrier_timeout_ns, cluster_rank(), cluster_size(), 0u, 0};
+  for (int phase = 0; phase < 2; ++phase) {
+    const int* order = phase == 0 ? order_h : order_l;
+    const int count = phase == 0 ? count_h : count_l;
+    int* queue = phase == 0 ? queue_h : queue_l;
+    bool ok = true;
+    for (;;) {
+      if (tm.leader()) sidx = atomicAdd(queue, 1);
+      if (!tm.sync()) {
+        ok = false;
+        break;
+      }
+      const int idx = *cluster_map(&sidx, 0u);
+      if (!tm.sync()) {  // every CTA has read rank 0's index before the next take
+        ok = false;
+        break;
+      }
+      if (idx >= count) break;
+      const int code = order[idx];
+      const int p = code & ((1 << kModeShift) - 1);
+      const Dev<T>& d = devs[p];
+      const unsigned long long t0 = gtimer();
+      batch_solve_one(tm, d, P, code >> kModeShift);
+      if (!tm.sync()) {
+        ok = false;
+        break;
+      }
+      if (tm.leader()) {
+        times[2 * p] = t0;
+        times[2 * p + 1] = gtimer();
+      }
+    }
+    if (!ok) break;
+  }
+  cluster_sync_all();
 }
 
 // Per-problem sizes and offsets.
@@ -188,6 +251,15 @@ struct osqp_batch {
   std::vector<int> mode;            // per-problem kernel mode for the next launch
   std::vector<unsigned long long> times_host;
   std::vector<double> last_dur;     // device seconds of problem i in its last launch (0: none)
+  std::vector<char> on_cluster;     // problem i was solved by a cluster in its last launch
+  // heavy-problem clusters beside the one-CTA kernel (whole-batch launches)
+  int cluster_ok = 0;               // the device can host a kBatchCluster-CTA cluster
+  cudaStream_t cstream = nullptr;
+  int* corder = nullptr;
+  int* cqueue = nullptr;
+  int* cerr = nullptr;
+  cudaEvent_t cfork = nullptr, cjoin = nullptr;
+  bool cused = false;
   bool unrecorded = false;          // a whole-batch launch whose times are not in last_dur
   char* arena = nullptr;
   size_t static_bytes = 0, arena_bytes = 0;
@@ -254,23 +326,97 @@ void fill_batch_devs(osqp_batch* b) {
   }
 }
 
+// Heavy problems of a whole-batch launch: with every problem's device time
+// from its previous launch known and more problems than CTAs, a problem
+// whose time exceeds the fair share (total time / CTAs, the wall time of a
+// perfectly balanced launch) would set the wall time on one SM; such
+// problems (longest first, at most kMaxHeavy) go to clusters.
+void pick_heavy(const osqp_batch* b, const std::vector<int>& sel, cudaStream_t st,
+                std::vector<int>& heavy, std::vector<int>& light) {
+  heavy.clear();
+  light = sel;
+  if (!b->cluster_ok || b->set.launch == 1 || st != b->stream || (int)sel.size() <= b->grid) return;
+  double total = 0.0;
+  for (int v : sel) {
+    if (!(b->last_dur[v] > 0.0)) return;
+    total += b->last_dur[v];
+  }
+  const double fair = total / b->grid;
+  light.clear();
+  for (int v : sel) {
+    if ((int)heavy.size() < kMaxHeavy && b->last_dur[v] > fair) heavy.push_back(v);
+    else light.push_back(v);
+  }
+}
+
 template <typename T>
 int launch_batch(osqp_batch* b, const std::vector<int>& sel, int* order_d, int* queue,
                  cudaStream_t st) {
-  const int count = (int)sel.size();
-  std::vector<int> code(count);
-  for (int k = 0; k < count; ++k) code[k] = sel[k] | (b->mode[sel[k]] << kModeShift);
-  if (cudaMemcpyAsync(order_d, code.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st) !=
-      cudaSuccess)
+  std::vector<int> heavy, light;
+  pick_heavy(b, sel, st, heavy, light);
+  const int nl = (int)light.size(), nh = (int)heavy.size();
+  const int nclusters = std::min(nh, kMaxHeavyClusters);
+  std::vector<int> code(nl), hcode(nh);
+  for (int k = 0; k < nl; ++k) code[k] = light[k] | (b->mode[light[k]] << kModeShift);
+  for (int k = 0; k < nh; ++k) hcode[k] = heavy[k] | (b->mode[heavy[k]] << kModeShift);
+  if (nl && cudaMemcpyAsync(order_d, code.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess)
     return OSQP_ERR_CUDA;
   // the host vector must outlive the copy: wait for it (small, pageable)
   if (cudaStreamSynchronize(st) != cudaSuccess) return OSQP_ERR_CUDA;
   if (cudaMemsetAsync(queue, 0, sizeof(int), st) != cudaSuccess) return OSQP_ERR_CUDA;
-  const int grid = std::max(1, std::min(b->grid, count));
-  k_batch<T><<<grid, kBatchThreads, 0, st>>>((const Dev<T>*)b->devs, order_d, count, b->P, queue,
-                                              b->times_d);
-  if (cudaGetLastError() != cudaSuccess) return OSQP_ERR_CUDA;
-  for (int v : sel) b->mode[v] = 0;
+  if (nh) {
+    if (!b->cstream) {
+      if (cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaMalloc((void**)&b->corder, sizeof(int) * b->count) != cudaSuccess ||
+          cudaMalloc((void**)&b->cqueue, sizeof(int)) != cudaSuccess ||
+          cudaMalloc((void**)&b->cerr, sizeof(int)) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->cfork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->cjoin, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return OSQP_ERR_CUDA;
+      }
+    }
+    // the cluster kernel also reads the light queue: fork after it is reset
+    if (cudaEventRecord(b->cfork, st) != cudaSuccess ||
+        cudaStreamWaitEvent(b->cstream, b->cfork, 0) != cudaSuccess ||
+        cudaMemcpyAsync(b->corder, hcode.data(), sizeof(int) * nh, cudaMemcpyHostToDevice,
+                        b->cstream) != cudaSuccess ||
+        cudaMemsetAsync(b->cqueue, 0, sizeof(int), b->cstream) != cudaSuccess ||
+        cudaMemsetAsync(b->cerr, 0, sizeof(int), b->cstream) != cudaSuccess ||
+        cudaStreamSynchronize(b->cstream) != cudaSuccess)
+      return OSQP_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nclusters * kBatchCluster);
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.stream = b->cstream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kBatchCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_batch_cluster<T>, (const Dev<T>*)b->devs, (const int*)b->corder,
+                           nh, b->cqueue, (const int*)order_d, nl, queue, b->P, b->times_d,
+                           b->cerr) != cudaSuccess ||
+        cudaEventRecord(b->cjoin, b->cstream) != cudaSuccess)
+      return OSQP_ERR_CUDA;
+  }
+  if (nl) {
+    // leave the clusters' SMs to them whichever kernel the GPU starts first
+    const int grid = std::max(1, std::min(b->grid - nclusters * kBatchCluster, nl));
+    k_batch<T><<<grid, kBatchThreads, 0, st>>>((const Dev<T>*)b->devs, order_d, nl, b->P, queue,
+                                                b->times_d);
+    if (cudaGetLastError() != cudaSuccess) return OSQP_ERR_CUDA;
+  }
+  if (nh && cudaStreamWaitEvent(st, b->cjoin, 0) != cudaSuccess) return OSQP_ERR_CUDA;
+  for (int v : sel) {
+    b->mode[v] = 0;
+    b->on_cluster[v] = 0;
+  }
+  for (int v : heavy) b->on_cluster[v] = 1;
+  if (st == b->stream) b->cused = nh > 0;
   return OSQP_OK;
 }
 
@@ -330,6 +476,12 @@ int batch_wait(osqp_batch* b, const std::vector<int>& sel) {
     b->last_time = ms * 1e-3;
   record_durations(b, sel);
   b->unrecorded = false;
+  if (b->cused) {
+    int e = 0;
+    if (cudaMemcpy(&e, b->cerr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return OSQP_ERR_CUDA;
+    if (e != kDevOk) return OSQP_ERR_DEVICE;
+  }
   return OSQP_OK;
 }
 
@@ -513,6 +665,25 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
   b->mode.assign(count, kModeScale);
   b->times_host.assign(2 * (size_t)count, 0);
   b->last_dur.assign(count, 0.0);
+  b->on_cluster.assign(count, 0);
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kBatchCluster);
+    cfg.blockDim = dim3(kBatchThreads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kBatchCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    const cudaError_t ec = settings->precision == OSQP_PRECISION_FP64
+                               ? cudaOccupancyMaxActiveClusters(&nc, k_batch_cluster<double>, &cfg)
+                               : cudaOccupancyMaxActiveClusters(&nc, k_batch_cluster<float>, &cfg);
+    if (ec != cudaSuccess) cudaGetLastError();
+    b->cluster_ok = ec == cudaSuccess && nc >= 1;
+  }
   if (cudaMemset(b->times_d, 0, sizeof(unsigned long long) * 2 * count) != cudaSuccess)
     return fail(OSQP_ERR_CUDA);
   b->order.resize(count);
@@ -715,7 +886,7 @@ int32_t osqp_batch_get(osqp_batch* b, int32_t i, double* x, double* y, double* z
     info->pcg_iters = s.pcg_iters;
     info->rho_updates = s.rho_updates;
     info->ruiz_passes = s.ruiz_passes;
-    info->launch = 1;
+    info->launch = b->on_cluster[i] ? 3 : 1;  // 3: solved by a cluster
     info->obj_val = s.obj;
     info->prim_res = s.prim_res;
     info->dual_res = s.dual_res;
@@ -739,7 +910,14 @@ int32_t osqp_batch_cleanup(osqp_batch* b) {
     if (S.queue) cudaFree(S.queue);
     if (S.done) cudaEventDestroy(S.done);
   }
-  void* ptrs[] = {b->arena, b->devs, b->order_d, b->queue, b->times_d};
+  if (b->cstream) {
+    if (cudaStreamSynchronize(b->cstream) != cudaSuccess) rc = OSQP_ERR_CUDA;
+    cudaStreamDestroy(b->cstream);
+  }
+  if (b->cfork) cudaEventDestroy(b->cfork);
+  if (b->cjoin) cudaEventDestroy(b->cjoin);
+  void* ptrs[] = {b->arena, b->devs, b->order_d, b->queue, b->times_d, b->corder, b->cqueue,
+                  b->cerr};
   for (void* p : ptrs)
     if (p && cudaFree(p) != cudaSuccess) rc = OSQP_ERR_CUDA;
   for (auto& ev : b->ev)

@@ -380,6 +380,122 @@ struct GridTeam {
   }
 };
 
+// Generic address of `p` (a shared variable of this CTA) in CTA `rank` of
+// the thread-block cluster (distributed shared memory).
+template <typename V>
+__device__ __forceinline__ V* cluster_map(V* p, unsigned rank) {
+  unsigned long long out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(p), "r"(rank));
+  return reinterpret_cast<V*>(out);
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// Hardware barrier over every thread of the cluster.  Used only where all
+// CTAs reach it unconditionally (kernel entry and exit).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
+// One thread-block cluster as a team (a problem too large for one SM and
+// too small to pay for whole-GPU barriers).  The barrier is a counter in
+// the shared memory of CTA 0 of the cluster, reached through distributed
+// shared memory: thread 0 of each CTA arrives with an acquire-release atomic
+// and spins with acquire loads, bounded by timeout_ns exactly like the grid
+// barrier (timeout → kDevBarrierTimeout and a poison add that releases every
+// waiter).  Reductions: each CTA reduces its block into its own shared
+// memory (double-buffered), and after the barrier every CTA combines the
+// cluster's partials in rank order, so all CTAs hold identical values.
+struct ClusterTeam {
+  static constexpr unsigned int kBarrierPoison = 0x80000000u;
+  double* sm;
+  double* cpart;  // [2][kMaxRed] this CTA's published block results
+  unsigned* ctr;  // barrier counter (CTA 0's is the one used)
+  int* err;
+  unsigned long long timeout_ns;
+  unsigned rank, csize, target;
+  int buf;
+
+  __device__ int nthreads() const { return (int)csize * blockDim.x; }
+  __device__ int tid() const { return (int)rank * blockDim.x + threadIdx.x; }
+  __device__ int nwarps() const { return (int)csize * (blockDim.x >> 5); }
+  __device__ int warp() const { return (int)rank * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+  __device__ bool leader() const { return rank == 0 && threadIdx.x == 0; }
+
+  __device__ bool sync() {
+    __syncthreads();
+    int* flag = reinterpret_cast<int*>(sm + 34 * kMaxRed - 1);
+    if (threadIdx.x == 0) {
+      target += csize;
+      unsigned* c0 = cluster_map(ctr, 0u);
+      unsigned c;
+      asm volatile("atom.acq_rel.gpu.add.u32 %0, [%1], 1;" : "=r"(c) : "l"(c0) : "memory");
+      c += 1u;
+      if (c < target) {
+        const unsigned long long t0 = gtimer();
+        unsigned int spins = 0;
+        for (;;) {
+          asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(c) : "l"(c0) : "memory");
+          if (c >= target) break;
+          if ((++spins & 255u) == 0 && gtimer() - t0 > timeout_ns) {
+            atomicExch(err, kDevBarrierTimeout);
+            atomicAdd(c0, kBarrierPoison);
+            c = kBarrierPoison;
+            break;
+          }
+        }
+      }
+      *flag = c < kBarrierPoison ? 1 : 0;
+    }
+    __syncthreads();
+    return *flag != 0;
+  }
+
+  template <int K, unsigned MAXMASK, typename V>
+  __device__ void publish(const V (&v)[K]) {
+    block_reduce<K, MAXMASK>(v, sm);
+    if (threadIdx.x < K) cpart[buf * kMaxRed + threadIdx.x] = sm[32 * kMaxRed + threadIdx.x];
+  }
+
+  // Combine the partials of the last publish (after a sync), in rank order.
+  template <int K, unsigned MAXMASK>
+  __device__ void collect(double (&out)[K]) {
+    if (threadIdx.x < K) {
+      const int k = threadIdx.x;
+      const bool mx = (MAXMASK >> k) & 1u;
+      double y[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        y[r] = r < (int)csize ? *cluster_map(cpart + buf * kMaxRed + k, (unsigned)r) : 0.0;
+      if (mx) {
+        unsigned long long x = dkey(y[0]);
+#pragma unroll
+        for (int r = 1; r < 16; ++r)
+          if (r < (int)csize) x = umax64(x, dkey(y[r]));
+        sm[33 * kMaxRed + k] = dunkey(x);
+      } else {
+        double x = y[0];
+#pragma unroll
+        for (int r = 1; r < 16; ++r)
+          if (r < (int)csize) x += y[r];
+        sm[33 * kMaxRed + k] = x;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = sm[33 * kMaxRed + k];
+    buf ^= 1;
+  }
+};
+
 struct BlockTeam {
   double* sm;
   __device__ int nthreads() const { return blockDim.x; }
@@ -646,8 +762,14 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
     tm.template publish<1, 0u>(sum);
     if (!tm.sync()) return false;
     tm.template collect<1, 0u>(sum);
-    const double mx = fmax(sum[0] / (double)n, qn[0]);
-    const double gamma = mx < kNormMin ? 1.0 : 1.0 / mx;
+    // In γ's max a norm below 1e-4 counts as 1 (a vanishing norm carries no
+    // scale, as for δ), and the max is clamped like the other norms; taken
+    // literally with q̄ = 0 and mostly-zero P̄ columns, 1/max would grow c
+    // geometrically pass after pass.
+    double mean = sum[0] / (double)n, qnv = qn[0];
+    if (mean < kNormMin) mean = 1.0;
+    if (qnv < kNormMin) qnv = 1.0;
+    const double gamma = 1.0 / fmin(fmax(fmax(mean, qnv), kNormMin), kNormMax);
     c *= gamma;
     if (dev[0] <= P.eps_equil) break;
   }

@@ -178,7 +178,7 @@ inline int check_settings(const osqp_settings& s) {
     return OSQP_ERR_SETTINGS;
   if (s.precision != OSQP_PRECISION_FP64 && s.precision != OSQP_PRECISION_FP32_MIXED)
     return OSQP_ERR_SETTINGS;
-  if (s.launch < 0 || s.launch > 2) return OSQP_ERR_SETTINGS;
+  if (s.launch < 0 || s.launch > 3) return OSQP_ERR_SETTINGS;
   return OSQP_OK;
 }
 

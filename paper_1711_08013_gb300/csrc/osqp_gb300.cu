@@ -72,6 +72,33 @@ __global__ void __launch_bounds__(kThreads) k_admm_grid(const __grid_constant__ 
   admm_stage(tm, d, P);
 }
 
+// Cluster-team kernels: one thread-block cluster of kClusterSize CTAs per
+// problem.  The counter is zeroed and every CTA has started before anyone
+// arrives at a team barrier, and no CTA leaves while another may still read
+// its shared memory (the two hardware cluster barriers, reached
+// unconditionally by every thread).
+#define OSQP_CLUSTER_KERNEL(NAME, STAGE_CALL, ...)                                      \
+  template <typename T>                                                                  \
+  __global__ void __launch_bounds__(kThreads) NAME(const __grid_constant__ Dev<T> d,     \
+                                                   const __grid_constant__ Params P,     \
+                                                   int* err, ##__VA_ARGS__) {            \
+    __shared__ double sm[kSmemDoubles];                                                  \
+    __shared__ double cpart[2 * kMaxRed];                                                \
+    __shared__ unsigned ctr;                                                             \
+    if (threadIdx.x == 0) ctr = 0u;                                                      \
+    cluster_sync_all();                                                                  \
+    ClusterTeam tm{sm, cpart, &ctr, err, P.barrier_timeout_ns, cluster_rank(),           \
+                   cluster_size(), 0u, 0};                                               \
+    STAGE_CALL;                                                                          \
+    cluster_sync_all();                                                                  \
+  }
+
+OSQP_CLUSTER_KERNEL(k_admm_cluster, admm_stage(tm, d, P))
+OSQP_CLUSTER_KERNEL(k_scale_cluster, scale_stage(tm, d, P, rho_bar, reset != 0), double rho_bar,
+                    int reset)
+OSQP_CLUSTER_KERNEL(k_refresh_cluster, refresh_stage(tm, d, P, rho_bar), double rho_bar)
+#undef OSQP_CLUSTER_KERNEL
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_admm_block(const __grid_constant__ Dev<T> d,
                                                           const __grid_constant__ Params P) {
@@ -87,6 +114,17 @@ __global__ void k_gather(double* __restrict__ dst, const int* __restrict__ idx,
     const int i = idx[k];
     dst[k] = i >= 0 ? src[i] : 0.0;
   }
+}
+
+// Barrier diagnostic: CTA `absent` returns without arriving, so the others
+// must time out, record the error and leave.
+__global__ void __launch_bounds__(kThreads) k_barrier_probe(Barrier* bar, int* err, double* part,
+                                                             unsigned long long timeout_ns,
+                                                             int absent) {
+  __shared__ double sm[kSmemDoubles];
+  GridTeam tm{bar, err, part, sm, timeout_ns, 0, 0u};
+  if ((int)blockIdx.x == absent) return;
+  tm.sync();
 }
 
 // warm start, part 1: x̄ = D⁻¹x, ȳ = cE⁻¹y, x̃ = x̄, δ = 0
@@ -153,8 +191,10 @@ __global__ void k_zero_iterates(const __grid_constant__ Dev<T> d) {
 // host side
 // ---------------------------------------------------------------------------
 
+constexpr int kClusterSize = 8;  // CTAs of a cluster team (portable maximum)
+
 struct osqp_solver {
-  int device = 0, num_sms = 0, grid = 0, use_grid = 0;
+  int device = 0, num_sms = 0, grid = 0, use_grid = 0, use_cluster = 0;
   cudaStream_t stream = nullptr;
   osqp_settings set{};
   Params P{};
@@ -249,10 +289,31 @@ Dev<float>& dev_of<float>(osqp_solver* s) {
   return s->d32;
 }
 
+// Launch a cluster-team kernel: one cluster of kClusterSize CTAs.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cluster(osqp_solver* s, void (*kernel)(KArgs...), Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterSize);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterSize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename T>
 int launch_scale(osqp_solver* s, int reset) {
   Dev<T>& d = dev_of<T>(s);
-  if (s->use_grid) {
+  if (s->use_cluster) {
+    CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    CK(launch_cluster(s, k_scale_cluster<T>, d, s->P, s->err, s->rho_bar, reset));
+  } else if (s->use_grid) {
     CK(cudaMemsetAsync(s->bar, 0, sizeof(Barrier), s->stream));
     CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
     double rb = s->rho_bar;
@@ -270,7 +331,10 @@ int launch_scale(osqp_solver* s, int reset) {
 template <typename T>
 int launch_refresh(osqp_solver* s) {
   Dev<T>& d = dev_of<T>(s);
-  if (s->use_grid) {
+  if (s->use_cluster) {
+    CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    CK(launch_cluster(s, k_refresh_cluster<T>, d, s->P, s->err, s->rho_bar));
+  } else if (s->use_grid) {
     CK(cudaMemsetAsync(s->bar, 0, sizeof(Barrier), s->stream));
     CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
     double rb = s->rho_bar;
@@ -292,7 +356,10 @@ int launch_admm(osqp_solver* s) {
     k_zero_iterates<T><<<64, 256, 0, s->stream>>>(d);
     CK(cudaGetLastError());
   }
-  if (s->use_grid) {
+  if (s->use_cluster) {
+    CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    CK(launch_cluster(s, k_admm_cluster<T>, d, s->P, s->err));
+  } else if (s->use_grid) {
     CK(cudaMemsetAsync(s->bar, 0, sizeof(Barrier), s->stream));
     CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
     void* args[] = {(void*)&d, (void*)&s->P, (void*)&s->bar, (void*)&s->err, (void*)&s->part};
@@ -394,7 +461,7 @@ int read_scalars(osqp_solver* s, Scalars* out) {
 }
 
 int check_device_error(osqp_solver* s) {
-  if (!s->use_grid) return OSQP_OK;
+  if (!s->use_grid && !s->use_cluster) return OSQP_OK;
   int e = 0;
   CK(cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
@@ -574,6 +641,29 @@ int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const 
   // grid of every SM slot the kernel can hold.
   const long long work = (long long)s->nnzKn + s->nnzA + n + m;
   s->use_grid = settings->launch == 2 || (settings->launch == 0 && work > 60000);
+  s->use_cluster = settings->launch == 3;
+  if (s->use_cluster) {
+    s->use_grid = 0;
+    // a cluster of kClusterSize one-SM CTAs must fit on the device
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClusterSize);
+    cfg.blockDim = dim3(kThreads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterSize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    cudaError_t ec = settings->precision == OSQP_PRECISION_FP64
+                         ? cudaOccupancyMaxActiveClusters(&nc, k_admm_cluster<double>, &cfg)
+                         : cudaOccupancyMaxActiveClusters(&nc, k_admm_cluster<float>, &cfg);
+    if (ec != cudaSuccess || nc < 1) {
+      cudaGetLastError();
+      return fail(OSQP_ERR_CUDA);
+    }
+  }
   int per_sm = 1;
   {
     int occ = 0;
@@ -601,7 +691,8 @@ int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const 
   }
   s->grid = s->num_sms * per_sm;
   {
-    const long long nwarps = (long long)(s->use_grid ? s->grid : 1) * (kThreads / 32);
+    const long long nwarps =
+        (long long)(s->use_grid ? s->grid : (s->use_cluster ? kClusterSize : 1)) * (kThreads / 32);
     s->kn_s = make_sched(s->kn_rp, nwarps);
     s->a_s = make_sched(s->a_rp, nwarps);
     s->kn_ci = to_positions(s->kn_s, s->kn_ci, -1);
@@ -640,7 +731,7 @@ int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const 
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(OSQP_ERR_CUDA);
   if ((rc = check_device_error(s))) return fail(rc);
   s->info.setup_time = elapsed_s(s->ev[0], s->ev[1]);
-  s->info.launch = s->use_grid ? 2 : 1;
+  s->info.launch = s->use_cluster ? 3 : (s->use_grid ? 2 : 1);
   *out = s;
   return OSQP_OK;
 }
@@ -803,6 +894,37 @@ int32_t osqp_get_certificate(osqp_solver* s, double* py, double* dx) {
   if (dx) CK(cudaMemcpyAsync(dx, out_dc(s), sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return OSQP_OK;
+}
+
+int32_t osqp_diag_barrier_timeout(double timeout_s) {
+  if (!(timeout_s > 0.0) || !(timeout_s <= 10.0)) return OSQP_ERR_ARG;
+  constexpr int kBlocks = 4;
+  char* mem = nullptr;
+  const size_t bytes = 256 + 256 + sizeof(double) * 2 * kBlocks * kMaxRed;
+  if (cudaMalloc((void**)&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return OSQP_ERR_CUDA;
+  }
+  Barrier* bar = (Barrier*)mem;
+  int* err = (int*)(mem + 256);
+  double* part = (double*)(mem + 512);
+  int rc = OSQP_OK;
+  if (cudaMemset(mem, 0, 512) != cudaSuccess) rc = OSQP_ERR_CUDA;
+  unsigned long long tns = (unsigned long long)(timeout_s * 1e9);
+  int absent = 1;
+  void* args[] = {&bar, &err, &part, &tns, &absent};
+  if (rc == OSQP_OK &&
+      cudaLaunchCooperativeKernel((const void*)k_barrier_probe, dim3(kBlocks), dim3(kThreads), args,
+                                  0, (cudaStream_t)0) != cudaSuccess)
+    rc = OSQP_ERR_CUDA;
+  if (rc == OSQP_OK && cudaDeviceSynchronize() != cudaSuccess) rc = OSQP_ERR_CUDA;
+  int e = 0;
+  if (rc == OSQP_OK && cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = OSQP_ERR_CUDA;
+  if (rc == OSQP_OK && e != kDevBarrierTimeout) rc = OSQP_ERR_DEVICE;
+  cudaGetLastError();
+  cudaFree(mem);
+  return rc;
 }
 
 int32_t osqp_cleanup(osqp_solver* s) {

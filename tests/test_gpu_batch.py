@@ -135,3 +135,27 @@ def test_batch_larger_mpc_mix():
     for i in range(0, len(qps), 37):
         prim, dual, ep, ed = acceptance(qps[i], res[i].x, res[i].y, 1e-3, 1e-3)
         assert prim <= ep * 1.01 and dual <= ed * 1.01
+
+
+def test_heavy_problems_on_clusters():
+    """More problems than CTAs and one problem far slower than the fair share:
+    once its time is known (second launch) it is solved by a cluster beside
+    the one-CTA kernel; every result still passes the acceptance test, and
+    the problems that stay on one CTA reproduce bit for bit."""
+    qps = pb.mpc_batch(300, seed=3150, nx_range=(4, 8), T_range=(5, 8))
+    qps.append(pb.mpc(32, 30, seed=5))
+    heavy = len(qps) - 1
+    with BatchSolver(qps) as bs:
+        bs.solve()
+        first = [bs.result(i) for i in range(len(qps))]
+        B.osqp_batch_reset(bs.handle)
+        bs.solve()
+        second = [bs.result(i) for i in range(len(qps))]
+    assert first[heavy].launch == 1 and second[heavy].launch == 3
+    assert sum(r.launch == 3 for r in second) <= 32
+    for i, r in enumerate(second):
+        assert r.status == B.SOLVED, i
+        prim, dual, ep, ed = acceptance(qps[i], r.x, r.y, 1e-3, 1e-3)
+        assert prim <= 1.01 * ep and dual <= 1.01 * ed, i
+        if r.launch == 1 and first[i].launch == 1:
+            assert np.array_equal(r.x, first[i].x), i

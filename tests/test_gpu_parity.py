@@ -47,7 +47,7 @@ def rel_err(a, b):
     return np.max(np.abs(a - b), initial=0.0) / max(1.0, np.max(np.abs(b), initial=0.0))
 
 
-@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("launch", [1, 2, 3], ids=["block", "grid", "cluster"])
 @pytest.mark.parametrize("iters", [1, 7, 40])
 @pytest.mark.parametrize("name,qp", CLASSES, ids=IDS)
 def test_step_parity_fp64(oracle_mod, name, qp, iters, launch):
@@ -63,7 +63,7 @@ def test_step_parity_fp64(oracle_mod, name, qp, iters, launch):
 
 
 @pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("launch", [1, 2, 3], ids=["block", "grid", "cluster"])
 @pytest.mark.parametrize("name,qp", CLASSES, ids=IDS)
 def test_end_to_end_eps_1e3(oracle_mod, name, qp, launch, precision):
     """ε = 1e-3: both results pass the acceptance test of §8 and the GPU
@@ -97,7 +97,7 @@ def test_high_accuracy_objective(oracle_mod, name, qp):
     assert prim <= ep * 1.01 and dual <= ed * 1.01
 
 
-@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("launch", [1, 2, 3], ids=["block", "grid", "cluster"])
 @pytest.mark.parametrize("seed", range(3))
 def test_primal_infeasible(launch, seed):
     qp = pb.primal_infeasible_qp(4, seed=seed)
@@ -108,7 +108,7 @@ def test_primal_infeasible(launch, seed):
     assert primal_cert_ok(qp, py, eps=1e-3)
 
 
-@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("launch", [1, 2, 3], ids=["block", "grid", "cluster"])
 @pytest.mark.parametrize("seed", range(3))
 def test_dual_infeasible(launch, seed):
     qp = pb.dual_infeasible_lp(3 + seed, seed=seed)
@@ -152,7 +152,7 @@ def _edge_cases():
 EDGE = _edge_cases()
 
 
-@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("launch", [1, 2, 3], ids=["block", "grid", "cluster"])
 @pytest.mark.parametrize("name,qp", EDGE, ids=[e[0] for e in EDGE])
 def test_edge_cases(oracle_mod, name, qp, launch):
     star = oracle_mod.solve(qp, **HIGH_ORACLE)
