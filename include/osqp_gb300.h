@@ -261,6 +261,12 @@ int32_t osqp_batch_slot_query(osqp_batch* b, int32_t slot);
 /* Wait for the slot's launch and retire it. */
 int32_t osqp_batch_slot_wait(osqp_batch* b, int32_t slot);
 
+/* 1 if a slot launch containing problem i solves its problems on clusters
+ * of 8 CTAs (problem i has at least 2^17 nonzeros in Kn = [P̄ Āᵀ] and Ā
+ * together, the device can host such a cluster and settings->launch ≠ 1),
+ * else 0.  A server may launch such problems on their own slots. */
+int32_t osqp_batch_uses_cluster(const osqp_batch* b, int32_t i);
+
 /* Device bytes that problem i occupies (its data, iterates and work arrays). */
 int64_t osqp_batch_footprint(const osqp_batch* b, int32_t i);
 

@@ -76,6 +76,7 @@ _SIGS = {
     "osqp_get_certificate": (C.c_int32, [_P, _P, _P]),
     "osqp_cleanup": (C.c_int32, [_P]),
     "osqp_diag_barrier_timeout": (C.c_int32, [C.c_double]),
+    "osqp_batch_uses_cluster": (C.c_int32, [_P, C.c_int32]),
     "osqp_batch_setup": (C.c_int32, [C.POINTER(_P), C.c_int32, _P, _P, _P, _P, _P,
                                      C.POINTER(osqp_settings), _P]),
     "osqp_batch_solve": (C.c_int32, [_P]),
@@ -322,6 +323,13 @@ def osqp_batch_slot_query(h, slot) -> bool:
 
 def osqp_batch_slot_wait(h, slot):
     _check(lib().osqp_batch_slot_wait(h, int(slot)), "osqp_batch_slot_wait")
+
+
+def osqp_batch_uses_cluster(h, i) -> bool:
+    v = lib().osqp_batch_uses_cluster(h, int(i))
+    if v < 0:
+        _check(int(v), "osqp_batch_uses_cluster")
+    return bool(v)
 
 
 def osqp_batch_footprint(h, i) -> int:

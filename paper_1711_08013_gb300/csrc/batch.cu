@@ -30,6 +30,8 @@ constexpr long long kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchCluster = 8;      // CTAs of a heavy-problem cluster
 constexpr int kMaxHeavyClusters = 4;  // clusters a launch may take for heavy problems
 constexpr int kMaxHeavy = 32;         // heavy problems per launch at most
+constexpr long long kClusterWork = 1 << 17;  // nonzeros of Kn + Ā from which a slot launch
+                                             // solves its problems on clusters
 
 enum : int { kModeScale = 1, kModeRefresh = 2, kModeReset = 4 };
 
@@ -272,6 +274,7 @@ struct osqp_batch {
     cudaStream_t stream = nullptr;
     int* order = nullptr;
     int* queue = nullptr;
+    int* err = nullptr;
     cudaEvent_t done = nullptr;
     std::vector<int> members;
   } slots[OSQP_BATCH_MAX_SLOTS];
@@ -349,9 +352,53 @@ void pick_heavy(const osqp_batch* b, const std::vector<int>& sel, cudaStream_t s
   }
 }
 
+// A slot launch (serving) solves its problems on clusters when one of them
+// is large: one CTA would hold such a problem for seconds.
+bool large_problem(const osqp_batch* b, int i) {
+  return (long long)b->L[i].nnz_kn + b->L[i].nnz_a >= kClusterWork;
+}
+
+template <typename T>
+int launch_slot_clusters(osqp_batch* b, const std::vector<int>& sel, int* order_d, int* queue,
+                         int* err, cudaStream_t st) {
+  const int k = (int)sel.size();
+  std::vector<int> code(k);
+  for (int j = 0; j < k; ++j) code[j] = sel[j] | (b->mode[sel[j]] << kModeShift);
+  if (cudaMemcpyAsync(order_d, code.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess ||
+      cudaMemsetAsync(queue, 0, sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(std::min(k, kMaxHeavyClusters) * kBatchCluster);
+  cfg.blockDim = dim3(kBatchThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kBatchCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_batch_cluster<T>, (const Dev<T>*)b->devs, (const int*)order_d, k,
+                         queue, (const int*)order_d, 0, queue, b->P, b->times_d, err) !=
+      cudaSuccess)
+    return OSQP_ERR_CUDA;
+  for (int v : sel) {
+    b->mode[v] = 0;
+    b->on_cluster[v] = 1;
+  }
+  return OSQP_OK;
+}
+
 template <typename T>
 int launch_batch(osqp_batch* b, const std::vector<int>& sel, int* order_d, int* queue,
-                 cudaStream_t st) {
+                 cudaStream_t st, int* slot_err = nullptr) {
+  if (slot_err && b->cluster_ok && b->set.launch != 1) {
+    for (int v : sel)
+      if (large_problem(b, v)) return launch_slot_clusters<T>(b, sel, order_d, queue, slot_err, st);
+  }
   std::vector<int> heavy, light;
   pick_heavy(b, sel, st, heavy, light);
   const int nl = (int)light.size(), nh = (int)heavy.size();
@@ -794,6 +841,7 @@ int32_t osqp_batch_launch(osqp_batch* b, int32_t slot, const int32_t* idx, int32
     if (cudaStreamCreateWithFlags(&S.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc((void**)&S.order, sizeof(int) * b->count) != cudaSuccess ||
         cudaMalloc((void**)&S.queue, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&S.err, sizeof(int)) != cudaSuccess ||
         cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       return OSQP_ERR_CUDA;
@@ -808,13 +856,21 @@ int32_t osqp_batch_launch(osqp_batch* b, int32_t slot, const int32_t* idx, int32
     for (int v : sel) b->mode[v] |= kModeReset;
   order_longest_first(b, sel);
   const int rc = b->set.precision == OSQP_PRECISION_FP64
-                     ? launch_batch<double>(b, sel, S.order, S.queue, S.stream)
-                     : launch_batch<float>(b, sel, S.order, S.queue, S.stream);
+                     ? launch_batch<double>(b, sel, S.order, S.queue, S.stream, S.err)
+                     : launch_batch<float>(b, sel, S.order, S.queue, S.stream, S.err);
   if (rc) return rc;
   if (cudaEventRecord(S.done, S.stream) != cudaSuccess) return OSQP_ERR_CUDA;
   for (int v : sel) b->inflight[v] = slot;
   S.members = sel;
   return OSQP_OK;
+}
+
+// Barrier timeout recorded by a cluster launch of the slot (0: none).
+static int slot_error(const osqp_batch::Slot& S) {
+  int e = 0;
+  if (S.err && cudaMemcpy(&e, S.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  return e == kDevOk ? OSQP_OK : OSQP_ERR_DEVICE;
 }
 
 static void retire(osqp_batch* b, int slot) {
@@ -836,8 +892,9 @@ int32_t osqp_batch_slot_query(osqp_batch* b, int32_t slot) {
   const cudaError_t e = cudaEventQuery(S.done);
   if (e == cudaErrorNotReady) return 0;
   if (e != cudaSuccess) return OSQP_ERR_CUDA;
+  const int rc = slot_error(S);
   retire(b, slot);
-  return 1;
+  return rc ? rc : 1;
 }
 
 int32_t osqp_batch_slot_wait(osqp_batch* b, int32_t slot) {
@@ -845,8 +902,14 @@ int32_t osqp_batch_slot_wait(osqp_batch* b, int32_t slot) {
   osqp_batch::Slot& S = b->slots[slot];
   if (S.members.empty()) return OSQP_OK;
   if (cudaEventSynchronize(S.done) != cudaSuccess) return OSQP_ERR_CUDA;
+  const int rc = slot_error(S);
   retire(b, slot);
-  return OSQP_OK;
+  return rc;
+}
+
+int32_t osqp_batch_uses_cluster(const osqp_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= b->count) return OSQP_ERR_ARG;
+  return (b->cluster_ok && b->set.launch != 1 && large_problem(b, i)) ? 1 : 0;
 }
 
 int64_t osqp_batch_footprint(const osqp_batch* b, int32_t i) {
@@ -908,6 +971,7 @@ int32_t osqp_batch_cleanup(osqp_batch* b) {
     }
     if (S.order) cudaFree(S.order);
     if (S.queue) cudaFree(S.queue);
+    if (S.err) cudaFree(S.err);
     if (S.done) cudaEventDestroy(S.done);
   }
   if (b->cstream) {

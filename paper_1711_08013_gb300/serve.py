@@ -7,6 +7,8 @@ start).  The loop admits arrived requests onto free launch slots — each slot
 is an independent stream, so requests that arrive while others are on the
 GPU start as soon as CTAs free up and their work overlaps on the device —
 as long as the device footprint of the work in flight stays within a budget.
+Large problems (solved by clusters of CTAs, see osqp_batch_uses_cluster)
+are launched alone on their slot.
 A problem ID has at most one request in flight; later requests for it wait.
 Host-side bookkeeping only: every numeric step runs in the library.
 """
@@ -63,6 +65,8 @@ class Server:
         self.bs = BatchSolver(qps, stream=stream, **settings)
         self.h = self.bs.handle
         self.footprint = [B.osqp_batch_footprint(self.h, i) for i in range(len(qps))]
+        # large problems run on clusters of CTAs: they are launched alone
+        self.large = [B.osqp_batch_uses_cluster(self.h, i) for i in range(len(qps))]
         self.budget = footprint_budget if footprint_budget is not None else sum(self.footprint)
         if prime:  # cold solve of every resident problem (setup phase)
             self.bs.solve()
@@ -116,6 +120,15 @@ class Server:
                 for r in pending:
                     if r.pid in inflight_ids or r.pid in ids:
                         continue
+                    if self.large[r.pid]:
+                        if take:
+                            continue
+                        if inflight_bytes + self.footprint[r.pid] > self.budget and inflight_bytes:
+                            continue
+                        take.append(r)
+                        ids.add(r.pid)
+                        add += self.footprint[r.pid]
+                        break
                     fp = self.footprint[r.pid]
                     if inflight_bytes + add + fp > self.budget and (take or inflight_bytes):
                         continue

@@ -81,3 +81,28 @@ def test_footprint_budget_limits_inflight_work():
         st = srv.run(clone(reqs))
     assert st.max_inflight_bytes <= budget
     assert st.requests == len(reqs)
+
+
+def test_large_requests_on_clusters():
+    """A large problem in the pool is solved by a cluster of CTAs on its own
+    slot while small requests keep flowing; its results pass the acceptance
+    test on the perturbed data, and it starts from its previous solution."""
+    qps = pool() + [pb.random_qp(300, seed=4300)]
+    big = len(qps) - 1
+    rng = np.random.default_rng(22)
+    reqs = poisson_requests(qps[:big], rate=1000.0, duration=0.05, seed=21)
+    for t in (0.0, 0.02):
+        q, l, u = pb.perturb_vectors(rng, qps[big], 0.05)
+        reqs.append(Request(big, t, q, l, u))
+    with Server(qps, slots=4) as srv:
+        assert srv.large[big] and not any(srv.large[:big])
+        st = srv.run(reqs, keep_x=True)
+        assert st.requests == len(reqs)
+        x, y, z, info = B.osqp_batch_get(srv.h, big, qps[big].n, qps[big].m)
+        assert info.launch == 3
+    for r in reqs:
+        assert r.status == B.SOLVED, (r.pid, r.status)
+    last = [r for r in reqs if r.pid == big][-1]
+    qp2 = pb._finish("req", qps[big].P, last.q, qps[big].A, last.l, last.u)
+    prim, dual, ep, ed = acceptance(qp2, last.x, y, 1e-3, 1e-3)
+    assert prim <= 1.01 * ep and dual <= 1.01 * ed
