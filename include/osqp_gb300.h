@@ -101,6 +101,17 @@ typedef struct {
                                     cooperative grid, 3 one thread-block cluster
                                     of 8 CTAs (OSQP_ERR_CUDA at setup if the
                                     device cannot host such a cluster) */
+  int32_t polish;                /* 1: solution polishing (§4) after a solved run:
+                                    active sets from the sign of y, the
+                                    δ-regularised reduced KKT system of Eq.
+                                    (kkt_polish_reg) solved by FP64 Jacobi-PCG in
+                                    eliminated form, iterative refinement (Eq.
+                                    iterative_refinement); the result replaces the
+                                    ADMM solution only when y has the signs of Eq.
+                                    (compl_slack) on the active rows and both
+                                    residuals are no larger.  Default 0 */
+  int32_t polish_refine_iter;    /* refinement passes, default 3 */
+  double delta;                  /* δ of Eq. (kkt_polish_reg), default 1e-6 */
 } osqp_settings;
 
 typedef struct {
@@ -111,6 +122,8 @@ typedef struct {
   double rho_estimate;
   double setup_time; /* seconds: scaling, ρ and Jacobi build (device events) */
   double solve_time; /* seconds: the ADMM iterations and unscaling (device events) */
+  int32_t polished;  /* 1 polished solution returned, -1 polishing rejected, 0 not run */
+  int32_t pad;
 } osqp_info;
 
 typedef struct osqp_solver osqp_solver;

@@ -36,6 +36,7 @@ class Settings(C.Structure):
         ("adaptive_rho_tolerance", C.c_double), ("eps_equil", C.c_double),
         ("max_iter", C.c_int), ("check_interval", C.c_int), ("adaptive_rho", C.c_int),
         ("scaling_iters", C.c_int), ("max_rho_updates", C.c_int), ("warm_start", C.c_int),
+        ("polish", C.c_int), ("polish_refine_iter", C.c_int), ("delta", C.c_double),
     ]
 
 
@@ -44,7 +45,7 @@ class Info(C.Structure):
         ("status", C.c_int), ("iter", C.c_int), ("rho_updates", C.c_int), ("ruiz_passes", C.c_int),
         ("obj_val", C.c_double), ("prim_res", C.c_double), ("dual_res", C.c_double),
         ("rho_bar", C.c_double), ("setup_time", C.c_double), ("solve_time", C.c_double),
-        ("nnz_L", C.c_longlong),
+        ("nnz_L", C.c_longlong), ("polished", C.c_int), ("pad", C.c_int),
     ]
 
 
@@ -52,7 +53,7 @@ class Info(C.Structure):
 DEFAULTS = dict(rho=0.1, sigma=1e-6, alpha=1.6, eps_abs=1e-3, eps_rel=1e-3, eps_pinf=1e-4,
                 eps_dinf=1e-4, adaptive_rho_tolerance=5.0, eps_equil=1e-3, max_iter=4000,
                 check_interval=25, adaptive_rho=1, scaling_iters=10, max_rho_updates=20,
-                warm_start=0)
+                warm_start=0, polish=0, polish_refine_iter=3, delta=1e-6)
 
 
 def build(force: bool = False) -> str:
@@ -109,6 +110,7 @@ class Result:
     solve_time: float
     nnz_L: int
     ruiz_passes: int
+    polished: int = 0
 
 
 def _i32(a):
@@ -140,7 +142,7 @@ def solve(qp, x0=None, y0=None, **overrides) -> Result:
         raise ValueError(f"oracle_solve rejected the problem (code {rc})")
     return Result(x, y, z, pc, dc, info.status, info.iter, info.rho_updates, info.obj_val,
                   info.prim_res, info.dual_res, info.rho_bar, info.setup_time, info.solve_time,
-                  int(info.nnz_L), info.ruiz_passes)
+                  int(info.nnz_L), info.ruiz_passes, info.polished)
 
 
 def ruiz(Pfull, q, A, l, u, scaling_iters=10, eps_equil=1e-3):

@@ -41,6 +41,9 @@ typedef struct {
   int scaling_iters;              /* upper bound on Ruiz passes (0 = no scaling) */
   int max_rho_updates;
   int warm_start;                 /* 1: x, y on input are the initial guess (§6) */
+  int polish;                     /* 1: solution polishing (§4) after a solved run */
+  int polish_refine_iter;         /* iterative-refinement passes of §4 (default 3) */
+  double delta;                   /* regularisation δ of Eq. kkt_polish_reg (default 1e-6) */
 } oracle_settings;
 
 typedef struct {
@@ -48,6 +51,8 @@ typedef struct {
   double obj_val, prim_res, dual_res, rho_bar;
   double setup_time, solve_time;
   long long nnz_L;
+  int polished;                   /* 1 accepted, -1 tried and rejected, 0 not tried */
+  int pad;
 } oracle_info;
 
 /* Solve min ½xᵀPx+qᵀx s.t. l ≤ Ax ≤ u.  P: upper triangle, CSC, n × n;

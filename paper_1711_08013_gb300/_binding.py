@@ -41,7 +41,8 @@ class osqp_settings(C.Structure):
         ("max_iter", C.c_int32), ("check_interval", C.c_int32), ("adaptive_rho", C.c_int32),
         ("scaling_iters", C.c_int32), ("max_rho_updates", C.c_int32),
         ("pcg_max_iter", C.c_int32), ("precision", C.c_int32), ("warm_start", C.c_int32),
-        ("launch", C.c_int32),
+        ("launch", C.c_int32), ("polish", C.c_int32), ("polish_refine_iter", C.c_int32),
+        ("delta", C.c_double),
     ]
 
 
@@ -51,6 +52,7 @@ class osqp_info(C.Structure):
         ("rho_updates", C.c_int32), ("ruiz_passes", C.c_int32), ("launch", C.c_int32),
         ("obj_val", C.c_double), ("prim_res", C.c_double), ("dual_res", C.c_double),
         ("rho_estimate", C.c_double), ("setup_time", C.c_double), ("solve_time", C.c_double),
+        ("polished", C.c_int32), ("pad", C.c_int32),
     ]
 
     def as_dict(self):

@@ -214,7 +214,8 @@ size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
   const size_t kn_v = b.take<T>(L.kn_s.npos);
   const size_t a_v = b.take<T>(L.a_s.npos);
   const size_t rt = b.take<uint8_t>(m);
-  size_t on[15], om[19], otn[11], otm[6];
+  const size_t pact = b.take<uint8_t>(m);
+  size_t on[22], om[22], otn[11], otm[6];
   for (auto& v : on) v = b.take<double>(n);
   for (auto& v : om) v = b.take<double>(m);
   for (auto& v : otn) v = b.take<T>(n);
@@ -224,13 +225,16 @@ size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
     d->kn_v = (T*)(base + kn_v);
     d->a_v = (T*)(base + a_v);
     d->rtype = (uint8_t*)(base + rt);
+    d->pol_act = (uint8_t*)(base + pact);
     double** nv[] = {&d->D, &d->q, &d->pdiag, &d->dg, &d->nrm_n, &d->x, &d->dx, &d->px,
-                     &d->aty, &d->pdx, &d->atdy, &d->x_out, &d->dcert, &d->xt, &d->Dinv};
-    for (int k = 0; k < 15; ++k) *nv[k] = (double*)(base + on[k]);
+                     &d->aty, &d->pdx, &d->atdy, &d->x_out, &d->dcert, &d->xt, &d->Dinv,
+                     &d->pol_x, &d->pol_dx, &d->pol_r, &d->pol_z, &d->pol_p, &d->pol_kp,
+                     &d->pol_dg};
+    for (int k = 0; k < 22; ++k) *nv[k] = (double*)(base + on[k]);
     double** mv[] = {&d->E, &d->l, &d->u, &d->rho, &d->rho_inv, &d->nrm_m, &d->z, &d->y,
                      &d->dy, &d->ax, &d->adx, &d->azt, &d->z_out, &d->y_out, &d->pcert,
-                     &d->zt, &d->wm, &d->um, &d->Einv};
-    for (int k = 0; k < 19; ++k) *mv[k] = (double*)(base + om[k]);
+                     &d->zt, &d->wm, &d->um, &d->Einv, &d->pol_y, &d->pol_t, &d->pol_r2};
+    for (int k = 0; k < 22; ++k) *mv[k] = (double*)(base + om[k]);
     T** tn[] = {&d->dinv, &d->b, &d->mr, &d->p, &d->r0, &d->r1, &d->s0, &d->s1, &d->w0, &d->w1,
                 &d->dxt};
     for (int k = 0; k < 11; ++k) *tn[k] = (T*)(base + otn[k]);
@@ -950,6 +954,7 @@ int32_t osqp_batch_get(osqp_batch* b, int32_t i, double* x, double* y, double* z
     info->rho_updates = s.rho_updates;
     info->ruiz_passes = s.ruiz_passes;
     info->launch = b->on_cluster[i] ? 3 : 1;  // 3: solved by a cluster
+    info->polished = s.polished;
     info->obj_val = s.obj;
     info->prim_res = s.prim_res;
     info->dual_res = s.dual_res;

@@ -69,6 +69,7 @@ struct Scalars {
   // continues from the current iterates takes its first PCG tolerance from
   // them (0: no check since the iterates were last reset)
   double rp_last, rd_last;
+  int polished, pad2;  // 1 polished, -1 rejected, 0 not run (§4)
 };
 
 struct Params {
@@ -76,6 +77,8 @@ struct Params {
   double pcg_kappa, pcg_floor, pcg_reduce, time_limit_ns;
   int max_iter, check_interval, adaptive_rho, scaling_iters, max_rho_updates, pcg_max_iter;
   unsigned long long barrier_timeout_ns;
+  int polish, polish_refine;  // §4 solution polishing
+  double delta;
 };
 
 template <typename T>
@@ -103,6 +106,11 @@ struct Dev {
   // x̃, z̃ once per ADMM iteration; working-precision copies of ρ and ρ⁻¹
   T *dxt, *dzt, *rhoT, *rho_invT;
   double *px, *aty, *pdx, *atdy, *ax, *adx, *azt;
+  // solution polishing (§4): n-vectors x, r, M⁻¹r, p, Kp, Jacobi diagonal;
+  // m-vectors y, Āp/δ (or the refinement's Ā-side terms), r₂; row states
+  double *pol_x, *pol_dx, *pol_r, *pol_z, *pol_p, *pol_kp, *pol_dg;
+  double *pol_y, *pol_t, *pol_r2;
+  uint8_t* pol_act;
   double *x_out, *y_out, *z_out, *pcert, *dcert;
   Scalars* sc;
 };
@@ -866,6 +874,234 @@ __device__ bool refresh_stage(Team& tm, const Dev<T>& d, const Params& P, double
 }
 
 // ---------------------------------------------------------------------------
+// Solution polishing (§4) in the scaled problem, after a solved run.  Active
+// sets from the sign of ȳ; the δ-regularised reduced KKT system of Eq.
+// (kkt_polish_reg) is solved in eliminated form,
+//   (P̄ + δI + δ⁻¹Ā_actᵀĀ_act) x = −q̄ + δ⁻¹Ā_actᵀ b,   y_act = (Ā_act x − b)/δ,
+// by FP64 Jacobi-PCG, and iterative refinement (Eq. iterative_refinement)
+// against the unregularised system runs polish_refine passes: with
+// r₂ = b − Ā_act x the correction Δx solves the same matrix with right-hand
+// side −q̄ − P̄x − Ā_actᵀ(y − r₂/δ), and Δy = (Ā_act Δx − r₂)/δ (formed from
+// the small correction, not from Ā_act x⁺ − b, which would lose the digits
+// that the division by δ magnifies).  Matrix
+// values are the raw FP64 ones scaled on the fly (c·D·P·D, E·A·D), so both
+// precision modes polish in FP64.  The candidate replaces the ADMM iterates
+// only when y has the signs of Eq. (compl_slack) on the active rows and its
+// unscaled residuals are no larger than the ADMM ones.  Returns false on a
+// failed team barrier; *pr_io, *dr_io, *obj_io receive the accepted
+// residuals and objective.
+// ---------------------------------------------------------------------------
+constexpr int kPolishPcgMax = 4000;
+constexpr double kPolishPcgTol = 1e-10;
+
+template <class Team, typename T>
+__device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Params& P,
+                                          double* pr_io, double* dr_io, double* obj_io) {
+  const int n = d.n, m = d.m, tid = tm.tid(), nth = tm.nthreads();
+  const double delta = P.delta, idelta = 1.0 / P.delta;
+  const double c = d.sc->c;
+  const double* __restrict__ D = d.D;
+  const double* __restrict__ E = d.E;
+  uint8_t* __restrict__ act = d.pol_act;
+  double* __restrict__ x = d.pol_x;
+  double* __restrict__ dxp = d.pol_dx;
+  double* __restrict__ r = d.pol_r;
+  double* __restrict__ zz = d.pol_z;
+  double* __restrict__ p = d.pol_p;
+  double* __restrict__ kp = d.pol_kp;
+  double* __restrict__ dg = d.pol_dg;
+  double* __restrict__ y = d.pol_y;
+  double* __restrict__ t = d.pol_t;
+  double* __restrict__ r2 = d.pol_r2;
+  auto bnd = [&](int i) { return act[i] == 1 ? d.l[i] : d.u[i]; };
+  // Ā v into out (row sums E_i Σ a_ij D_j v_j; long rows pre-zeroed)
+  auto a_times = [&](const double* v, double* out) {
+    spmv<1, false, double, double>(
+        tm, d.as, d.a_ci, d.a_raw, [&](int col, double a, double* acc) { acc[0] += a * D[col] * v[col]; },
+        [&](int i, double* acc) { out[i] = E[i] * acc[0]; },
+        [&](int i, int, double* acc) { atomicAdd(&out[i], E[i] * acc[0]); });
+  };
+  // Kn·[v; w] = P̄v + Āᵀw, handed per row (or long-row chunk) to emit(j, first, value)
+  auto kn_times = [&](const double* v, const double* w, auto emit_row, auto emit_chunk) {
+    spmv<2, false, double, double>(
+        tm, d.kn, d.kn_ci, d.kn_raw,
+        [&](int col, double a, double* acc) {
+          if (col < n) acc[0] += a * D[col] * v[col];
+          else acc[1] += a * E[col - n] * w[col - n];
+        },
+        [&](int j, double* acc) { emit_row(j, c * D[j] * acc[0], D[j] * acc[1]); },
+        [&](int j, int first, double* acc) { emit_chunk(j, first, c * D[j] * acc[0], D[j] * acc[1]); });
+  };
+
+  // active sets, zero start, Jacobi diagonal P̄_jj + δ + δ⁻¹Σ_act Ā_ij²
+  for (int i = tid; i < m; i += nth) {
+    const double yi = d.y[i];
+    const uint8_t ty = d.rtype[i];
+    act[i] = (yi < 0.0 && !(ty & kLInf)) ? 1 : ((yi > 0.0 && !(ty & kUInf)) ? 2 : 0);
+    y[i] = 0.0;
+  }
+  for (int j = tid; j < n; j += nth) {
+    x[j] = 0.0;
+    dg[j] = 0.0;
+  }
+  zero_long(tm, d.as, t);
+  zero_long(tm, d.kn, r);
+  if (!tm.sync()) return false;
+  spmv<1, false, double, double>(
+      tm, d.kn, d.kn_ci, d.kn_raw,
+      [&](int col, double a, double* acc) {
+        if (col >= n && act[col - n]) {
+          const double e = E[col - n] * a;
+          acc[0] += e * e;
+        }
+      },
+      [&](int j, double* acc) { dg[j] = d.pdiag[j] + delta + idelta * D[j] * D[j] * acc[0]; },
+      [&](int j, int first, double* acc) {
+        atomicAdd(&dg[j], idelta * D[j] * D[j] * acc[0] + (first ? d.pdiag[j] + delta : 0.0));
+      });
+  if (!tm.sync()) return false;
+
+  for (int pass = 0; pass <= P.polish_refine; ++pass) {
+    // r₂ = b − Ā_act x and the weights y − r₂/δ of the right-hand side
+    a_times(x, t);
+    if (!tm.sync()) return false;
+    for (int i = tid; i < m; i += nth) {
+      const double ri = act[i] ? bnd(i) - t[i] : 0.0;
+      r2[i] = ri;
+      t[i] = act[i] ? y[i] - ri * idelta : 0.0;
+    }
+    if (!tm.sync()) return false;
+    // rhs = −q̄ − P̄x − Āᵀ(y − r₂/δ) into r
+    kn_times(
+        x, t, [&](int j, double pv, double av) { r[j] = -d.q[j] - pv - av; },
+        [&](int j, int first, double pv, double av) {
+          atomicAdd(&r[j], -pv - av - (first ? d.q[j] : 0.0));
+        });
+    zero_long(tm, d.kn, kp);
+    if (!tm.sync()) return false;
+    zero_long(tm, d.as, t);
+    // PCG for the correction Δx from zero
+    double red[2] = {0.0, 0.0};  // (r, M⁻¹r), ‖r‖∞
+    for (int j = tid; j < n; j += nth) {
+      const double zj = r[j] / dg[j];
+      dxp[j] = 0.0;
+      zz[j] = zj;
+      p[j] = zj;
+      red[0] += r[j] * zj;
+      red[1] = fmax(red[1], fabs(r[j]));
+    }
+    tm.template publish<2, 2u>(red);
+    if (!tm.sync()) return false;
+    tm.template collect<2, 2u>(red);
+    double rz = red[0];
+    const double tol = kPolishPcgTol * red[1];
+    bool done = !(red[1] > tol) || !(rz > 0.0);
+    for (int it = 0; !done && it < kPolishPcgMax; ++it) {
+      // t = δ⁻¹Ā_act p
+      spmv<1, false, double, double>(
+          tm, d.as, d.a_ci, d.a_raw,
+          [&](int col, double a, double* acc) { acc[0] += a * D[col] * p[col]; },
+          [&](int i, double* acc) { t[i] = act[i] ? idelta * E[i] * acc[0] : 0.0; },
+          [&](int i, int, double* acc) {
+            if (act[i]) atomicAdd(&t[i], idelta * E[i] * acc[0]);
+          });
+      if (!tm.sync()) return false;
+      // Kp = P̄p + δp + Āᵀt and pᵀKp = pᵀP̄p + δ‖p‖² + δ‖t‖²
+      double g[1] = {0.0};
+      kn_times(
+          p, t,
+          [&](int j, double pv, double av) {
+            kp[j] = pv + av + delta * p[j];
+            g[0] += p[j] * pv + delta * p[j] * p[j];
+          },
+          [&](int j, int first, double pv, double av) {
+            atomicAdd(&kp[j], pv + av + (first ? delta * p[j] : 0.0));
+            g[0] += p[j] * pv + (first ? delta * p[j] * p[j] : 0.0);
+          });
+      for (int i = tid; i < m; i += nth) g[0] += delta * t[i] * t[i];
+      tm.template publish<1, 0u>(g);
+      if (!tm.sync()) return false;
+      tm.template collect<1, 0u>(g);
+      if (!(g[0] > 0.0)) break;
+      const double alpha_c = rz / g[0];
+      double red2[2] = {0.0, 0.0};
+      for (int j = tid; j < n; j += nth) {
+        dxp[j] += alpha_c * p[j];
+        const double rj = r[j] - alpha_c * kp[j];
+        r[j] = rj;
+        const double zj = rj / dg[j];
+        zz[j] = zj;
+        red2[0] += rj * zj;
+        red2[1] = fmax(red2[1], fabs(rj));
+      }
+      zero_long(tm, d.as, t);
+      tm.template publish<2, 2u>(red2);
+      if (!tm.sync()) return false;
+      tm.template collect<2, 2u>(red2);
+      if (!(red2[1] > tol) || !(red2[0] > 0.0)) break;
+      const double beta_c = red2[0] / rz;
+      rz = red2[0];
+      for (int j = tid; j < n; j += nth) p[j] = zz[j] + beta_c * p[j];
+      zero_long(tm, d.kn, kp);
+      if (!tm.sync()) return false;
+    }
+    if (!tm.sync()) return false;
+    // x ← x + Δx, y ← y + (Ā_act Δx − r₂)/δ
+    zero_long(tm, d.as, t);
+    if (!tm.sync()) return false;
+    a_times(dxp, t);
+    for (int j = tid; j < n; j += nth) x[j] += dxp[j];
+    if (!tm.sync()) return false;
+    for (int i = tid; i < m; i += nth)
+      if (act[i]) y[i] += (t[i] - r2[i]) * idelta;
+    zero_long(tm, d.as, t);
+    zero_long(tm, d.kn, r);
+    if (!tm.sync()) return false;
+  }
+
+  // acceptance: signs of y on the active rows, unscaled residuals
+  zero_long(tm, d.kn, kp);
+  if (!tm.sync()) return false;
+  a_times(x, t);
+  double chk[4] = {0.0, 0.0, 0.0, 0.0};  // prim, dual·c, sign violation, c·objective
+  kn_times(
+      x, y,
+      [&](int j, double pv, double av) {
+        kp[j] = pv + av;
+        chk[3] += x[j] * (0.5 * pv + d.q[j]);
+      },
+      [&](int j, int first, double pv, double av) {
+        atomicAdd(&kp[j], pv + av);
+        chk[3] += x[j] * (0.5 * pv + (first ? d.q[j] : 0.0));
+      });
+  if (!tm.sync()) return false;
+  for (int i = tid; i < m; i += nth) {
+    const double zi = fmin(fmax(t[i], d.l[i]), d.u[i]);
+    chk[0] = fmax(chk[0], fabs((t[i] - zi) / E[i]));
+    if (!(d.rtype[i] & kEq) && ((act[i] == 1 && y[i] > 0.0) || (act[i] == 2 && y[i] < 0.0)))
+      chk[2] = 1.0;
+  }
+  for (int j = tid; j < n; j += nth) chk[1] = fmax(chk[1], fabs((kp[j] + d.q[j]) / D[j]));
+  tm.template publish<4, 7u>(chk);
+  if (!tm.sync()) return false;
+  tm.template collect<4, 7u>(chk);
+  const double pr = chk[0], dr = chk[1] / c;
+  const bool accept = chk[2] == 0.0 && pr <= *pr_io && dr <= *dr_io;
+  if (accept) {
+    for (int j = tid; j < n; j += nth) d.x[j] = x[j];
+    for (int i = tid; i < m; i += nth) {
+      d.z[i] = fmin(fmax(t[i], d.l[i]), d.u[i]);
+      d.y[i] = y[i];
+    }
+    *pr_io = pr;
+    *dr_io = dr;
+    *obj_io = chk[3] / c;
+  }
+  if (tm.leader()) d.sc->polished = accept ? 1 : -1;
+  return tm.sync();
+}
+
+// ---------------------------------------------------------------------------
 // Stage 2: Algorithm 1 with the indirect linear solve of §3.1.
 // ---------------------------------------------------------------------------
 template <class Team, typename T>
@@ -1316,6 +1552,13 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     }
   }
   if (status == kUnsolved && P.max_iter > 0) status = kMaxIter;
+
+  // --- solution polishing (§4)
+  if (P.polish && status == kSolved) {
+    if (!polish_stage(tm, d, P, &prim_res, &dual_res, &obj)) return false;
+  } else if (tm.leader()) {
+    d.sc->polished = 0;
+  }
 
   // --- unscale (Eq. pb:scaled_qp) and certificates (§5.1)
   for (int j = tid; j < n; j += nth) {

@@ -141,6 +141,9 @@ inline Params make_params(const osqp_settings& s) {
   P.max_rho_updates = s.max_rho_updates;
   P.pcg_max_iter = s.pcg_max_iter;
   P.barrier_timeout_ns = 2000000000ull;
+  P.polish = s.polish;
+  P.polish_refine = s.polish_refine_iter;
+  P.delta = s.delta;
   return P;
 }
 
@@ -179,6 +182,8 @@ inline int check_settings(const osqp_settings& s) {
   if (s.precision != OSQP_PRECISION_FP64 && s.precision != OSQP_PRECISION_FP32_MIXED)
     return OSQP_ERR_SETTINGS;
   if (s.launch < 0 || s.launch > 3) return OSQP_ERR_SETTINGS;
+  if (s.polish < 0 || s.polish > 1 || s.polish_refine_iter < 0 || !(s.delta > 0))
+    return OSQP_ERR_SETTINGS;
   return OSQP_OK;
 }
 

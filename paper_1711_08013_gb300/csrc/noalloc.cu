@@ -106,7 +106,7 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   const size_t ch_kn = nkn / kChunk + nkn / 257 + 1, lr_kn = nkn / 257 + 1;
   const size_t ch_a = na / kChunk + na / 257 + 1, lr_a = na / 257 + 1;
   const size_t nr = n > m ? n : m;
-  constexpr int kSlots = 96;  // ≥ the number of take() calls below (82)
+  constexpr int kSlots = 96;  // ≥ the number of take() calls below (93)
   size_t o[kSlots];
   int c = 0;
   o[c++] = L.template take<int>(n + 1);       // 0 kn rp
@@ -138,7 +138,9 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   o[c++] = L.template take<int>(kMaxBins + 2);  // 26 bin starts
   o[c++] = L.template take<int>(nr + 2);      // 27 slice widths / starts
   o[c++] = L.template take<uint8_t>(m);       // 28 rtype
-  const int nvec_n = 15, nvec_m = 19;
+  const int at_pact = c;
+  o[c++] = L.template take<uint8_t>(m);       // 29 polishing row states
+  const int nvec_n = 22, nvec_m = 22;
   const int first_n = c;
   for (int k = 0; k < nvec_n; ++k) o[c++] = L.template take<double>(n);
   const int first_m = c;
@@ -151,7 +153,7 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   o[c++] = L.template take<Scalars>(1);
   const int at_err = c;
   o[c++] = L.template take<int>(2);
-  static_assert(29 + 15 + 19 + 11 + 6 + 2 <= kSlots, "scratch slot table too small");
+  static_assert(30 + 22 + 22 + 11 + 6 + 2 <= kSlots, "scratch slot table too small");
   if (base && p) {
     Dev<T>& d = p->d;
     d.n = in.n;
@@ -173,12 +175,15 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
     p->bin_start = (int*)(base + o[26]);
     p->wsum = (int*)(base + o[27]);
     d.rtype = (uint8_t*)(base + o[28]);
+    d.pol_act = (uint8_t*)(base + o[at_pact]);
     double** nv[] = {&d.D, &d.q, &d.pdiag, &d.dg, &d.nrm_n, &d.x, &d.dx, &d.px,
-                     &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt, &d.Dinv};
+                     &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt, &d.Dinv,
+                     &d.pol_x, &d.pol_dx, &d.pol_r, &d.pol_z, &d.pol_p, &d.pol_kp,
+                     &d.pol_dg};
     for (int k = 0; k < nvec_n; ++k) *nv[k] = (double*)(base + o[first_n + k]);
     double** mv[] = {&d.E, &d.l, &d.u, &d.rho, &d.rho_inv, &d.nrm_m, &d.z, &d.y, &d.dy,
                      &d.ax, &d.adx, &d.azt, &d.z_out, &d.y_out, &d.pcert, &d.zt, &d.wm, &d.um,
-                     &d.Einv};
+                     &d.Einv, &d.pol_y, &d.pol_t, &d.pol_r2};
     for (int k = 0; k < nvec_m; ++k) *mv[k] = (double*)(base + o[first_m + k]);
     T** tv[] = {&d.dinv, &d.b, &d.mr, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1, &d.dxt};
     for (int k = 0; k < 11; ++k) *tv[k] = (T*)(base + o[first_tn + k]);
@@ -591,7 +596,8 @@ extern "C" int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_col
       s.check_interval < 1 || s.scaling_iters < 0 || s.pcg_max_iter < 1 ||
       !(s.eps_abs >= 0) || !(s.eps_rel >= 0) || !(s.eps_pinf > 0) || !(s.eps_dinf > 0) ||
       !(s.adaptive_rho_tolerance >= 1) || !(s.pcg_tol_fraction >= 0) || !(s.pcg_tol_floor >= 0) ||
-      (s.precision != OSQP_PRECISION_FP64 && s.precision != OSQP_PRECISION_FP32_MIXED))
+      (s.precision != OSQP_PRECISION_FP64 && s.precision != OSQP_PRECISION_FP32_MIXED) ||
+      s.polish < 0 || s.polish > 1 || s.polish_refine_iter < 0 || !(s.delta > 0))
     return OSQP_ERR_SETTINGS;
   NaInput in{n, m, P_nnz, A_nnz, P_colptr, P_rowind, P_val, q, A_colptr, A_rowind, A_val,
              l, u, x, y};
@@ -628,6 +634,9 @@ extern "C" int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_col
   P.max_rho_updates = s.max_rho_updates;
   P.pcg_max_iter = s.pcg_max_iter;
   P.barrier_timeout_ns = 2000000000ull;
+  P.polish = s.polish;
+  P.polish_refine = s.polish_refine_iter;
+  P.delta = s.delta;
   cudaStream_t st = (cudaStream_t)stream;
   if (s.precision == OSQP_PRECISION_FP64)
     k_noalloc<double><<<1, kThreads, 0, st>>>(in, P, s.rho, base);
@@ -658,6 +667,7 @@ extern "C" int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_col
     info->prim_res = sc.prim_res;
     info->dual_res = sc.dual_res;
     info->rho_estimate = sc.rho_bar;
+    info->polished = sc.polished;
   }
   return OSQP_OK;
 }

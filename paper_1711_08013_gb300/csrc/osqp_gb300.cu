@@ -265,12 +265,15 @@ void fill_dev(osqp_solver* s, Arena& A, Dev<T>& d) {
   d.u_raw = A.take<double>(m);
   d.rtype = A.take<uint8_t>(m);
   double** nvec[] = {&d.D, &d.q, &d.pdiag, &d.dg, &d.nrm_n, &d.x, &d.dx, &d.px,
-                     &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt, &d.Dinv};
+                     &d.aty, &d.pdx, &d.atdy, &d.x_out, &d.dcert, &d.xt, &d.Dinv,
+                     &d.pol_x, &d.pol_dx, &d.pol_r, &d.pol_z, &d.pol_p, &d.pol_kp,
+                     &d.pol_dg};
   for (double** p : nvec) *p = A.take<double>(n);
   double** mvec[] = {&d.E, &d.l, &d.u, &d.rho, &d.rho_inv, &d.nrm_m, &d.z, &d.y,
                      &d.dy, &d.ax, &d.adx, &d.azt, &d.z_out, &d.y_out, &d.pcert,
-                     &d.zt, &d.wm, &d.um, &d.Einv};
+                     &d.zt, &d.wm, &d.um, &d.Einv, &d.pol_y, &d.pol_t, &d.pol_r2};
   for (double** p : mvec) *p = A.take<double>(m);
+  d.pol_act = A.take<uint8_t>(m);
   T** tn[] = {&d.dinv, &d.b, &d.mr, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1};
   for (T** p : tn) *p = A.take<T>(n);
   T** tmv[] = {&d.rt0, &d.rt1, &d.ap, &d.dzt, &d.rhoT, &d.rho_invT};
@@ -581,6 +584,9 @@ void osqp_set_default_settings(osqp_settings* s) {
   s->precision = OSQP_PRECISION_FP64;
   s->warm_start = 1;
   s->launch = 0;
+  s->polish = 0;
+  s->polish_refine_iter = 3;
+  s->delta = 1e-6;
 }
 
 const char* osqp_error_message(int32_t code) {
@@ -759,6 +765,7 @@ static int32_t refresh_info(osqp_solver* s) {
   s->info.obj_val = sc.obj;
   s->info.prim_res = sc.prim_res;
   s->info.dual_res = sc.dual_res;
+  s->info.polished = sc.polished;
   s->info.rho_estimate = sc.rho_bar;
   s->info.solve_time = s->solved ? elapsed_s(s->ev[2], s->ev[3]) : 0.0;
   s->rho_bar = sc.rho_bar;

@@ -24,6 +24,7 @@ class Result:
     setup_time: float
     solve_time: float
     launch: int
+    polished: int = 0
 
 
 class Solver:
@@ -42,7 +43,7 @@ class Solver:
         x, y, z, info = B.osqp_get_solution(self.handle, self.n, self.m)
         return Result(x, y, z, info.status, info.iter, info.pcg_iters, info.rho_updates,
                       info.obj_val, info.prim_res, info.dual_res, info.rho_estimate,
-                      info.setup_time, info.solve_time, info.launch)
+                      info.setup_time, info.solve_time, info.launch, info.polished)
 
     def certificate(self):
         return B.osqp_get_certificate(self.handle, self.n, self.m)
@@ -102,7 +103,7 @@ class BatchSolver:
         x, y, z, info = B.osqp_batch_get(self.handle, i, n, m)
         return Result(x, y, z, info.status, info.iter, info.pcg_iters, info.rho_updates,
                       info.obj_val, info.prim_res, info.dual_res, info.rho_estimate,
-                      info.setup_time, info.solve_time, info.launch)
+                      info.setup_time, info.solve_time, info.launch, info.polished)
 
     def close(self):
         if self.handle:
