@@ -42,6 +42,9 @@ WORKLOADS = {
                      "launch (cold: scaling + ADMM per problem)"),
     "serve": (4, "serving: Poisson arrivals at 2000 req/s over a pool of 256 random-QP (m=10n) and "
                  "256 Huber (100n x n) problem IDs, n~logU[10,NMAX], warm-started perturbed q/l/u"),
+    "svm": (None, "SVM QP (App. A.7): 100 features, 10000 points at 15% density, labels split in half; "
+                  "variables (x,t) n=10100, rows m=20000"),
+    "eqqp": (None, "equality-constrained QP (App. A.2): n=1000, m=500, P=MM^T+1e-2 I, A at 15%"),
     "lasso_path": (None, "Lasso regularisation path: the 20000x200 Lasso QP, 100 lambda values "
                          "log-spaced from |Ad^T b|_inf to 0.01 of it, q updated in place, warm start"),
     "mpc_loop": (None, "MPC closed loop: nx=80, nu=40, T=10 (App. A.3 instance ranges, DARE terminal "
@@ -157,6 +160,10 @@ def admm_bytes(n, m, nnz_kn, nnz_a, sv, K, J, C):
 
 def build_problem(args, rank):
     cfg, desc = WORKLOADS[args.workload]
+    if args.workload == "svm":
+        return cfg, desc, pb.svm(100, seed=7000 + rank)
+    if args.workload == "eqqp":
+        return cfg, desc, pb.eq_qp(1000, seed=8000 + rank)
     return cfg, desc, pb.config_problem(cfg, instance=rank)
 
 

@@ -215,13 +215,18 @@ def test_update_rho_still_converges():
     assert g.status == B.SOLVED and abs(g.rho_estimate - 3.0) < 1e-12
 
 
+FULL = {0: lambda: pb.config_problem(0), 1: lambda: pb.config_problem(1),
+        2: lambda: pb.config_problem(2), "svm": lambda: pb.svm(100, seed=7000),
+        "eqqp": lambda: pb.eq_qp(1000, seed=8000)}
+
+
 @pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("config", [0, 1, 2])
+@pytest.mark.parametrize("config", list(FULL))
 def test_configs_full_size(oracle_mod, config, precision):
     """The single-problem workloads at full size in the launch shape the
     benchmark uses (automatic): acceptance at ε = 1e-3 and the objective
     inside the convexity interval around the oracle's high-accuracy optimum."""
-    qp = pb.config_problem(config)
+    qp = FULL[config]()
     star = oracle_mod.solve(qp, eps_abs=1e-7, eps_rel=1e-7, max_iter=200000)
     with Solver(qp, precision=precision) as s:
         g = s.solve()
