@@ -53,6 +53,13 @@ WORKLOADS = {
                            "mu update, monthly D/F value update (same pattern), warm start"),
 }
 PARAM_LEN = {"lasso_path": 100, "mpc_loop": 100, "portfolio_bt": 960}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant kernel, from one ncu capture of the same command with the
+# kernels as they are now; for the batch, the capture of the first 608
+# problems scaled by the problems of the launch.  Absent: not captured.
+TRAFFIC = {("lasso", "fp64"): 19.997952e6, ("lasso", "fp32"): 14.182912e6,
+           ("random", "fp64"): 0.353792e6}
+TRAFFIC_BATCH_PER_PROBLEM = {"fp32": 91.059199e9 / 608}
 # Mean time per QP and mean iterations per QP that the paper reports for the
 # same sequences (OSQP direct method on a CPU; context only)
 PARAM_PAPER = {
@@ -358,7 +365,9 @@ def batch_main(args, ws, rank, local):
         "pcg_iters_per_solve": sum(r.pcg_iters for r in last) / count,
         "roofline": {"bound": "hbm", "kernel": "k_batch", "achieved": bytes_launch / t_launch / 1e9,
                      "peak": peak, "unit": "GB/s", "frac": bytes_launch / t_launch / 1e9 / peak,
-                     "traffic": None, "algorithmic_bytes_per_launch": bytes_launch},
+                     "traffic": (TRAFFIC_BATCH_PER_PROBLEM[args.precision] * count
+                                 if args.precision in TRAFFIC_BATCH_PER_PROBLEM else None),
+                     "algorithmic_bytes_per_launch": bytes_launch},
         "e2e": {"value": ws * count * e2e_steps / e2e_dt, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * sum(q.n + 2 * q.m for q in qps),
                 "d2h_bytes_per_step": 8 * sum(q.n + q.m for q in qps)},
@@ -687,8 +696,12 @@ def main():
         "admm_iters_per_solve": K_avg,
         "pcg_iters_per_solve": J_avg,
         "admm_kernel_ms": 1e3 * t_admm,
-        "roofline": {"bound": "hbm", "kernel": "k_admm_grid", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+        "roofline": {"bound": "hbm",
+                     "kernel": {1: "k_admm_block", 2: "k_admm_grid", 3: "k_admm_cluster"}.get(
+                         infos[-1].launch, "k_admm_grid"),
+                     "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": TRAFFIC.get((args.workload, args.precision)),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_launch},
         "e2e": {"value": ws * args.steps / e2e_dt, "unit": UNIT,
