@@ -59,7 +59,7 @@ PARAM_LEN = {"lasso_path": 100, "mpc_loop": 100, "portfolio_bt": 960}
 # problems scaled by the problems of the launch.  Absent: not captured.
 TRAFFIC = {("lasso", "fp64"): 19.997952e6, ("lasso", "fp32"): 14.182912e6,
            ("random", "fp64"): 0.353792e6}
-TRAFFIC_BATCH_PER_PROBLEM = {"fp32": 91.059199e9 / 608}
+TRAFFIC_BATCH_PER_PROBLEM = {"fp32": 101.408774e9 / 608}
 # Mean time per QP and mean iterations per QP that the paper reports for the
 # same sequences (OSQP direct method on a CPU; context only)
 PARAM_PAPER = {

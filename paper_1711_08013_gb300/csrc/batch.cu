@@ -30,6 +30,8 @@ constexpr long long kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchCluster = 8;      // CTAs of a heavy-problem cluster
 constexpr int kMaxHeavyClusters = 4;  // clusters a launch may take for heavy problems
 constexpr int kMaxHeavy = 32;         // heavy problems per launch at most
+constexpr size_t kPrefetchBytes = 512 << 10;  // matrix bytes above which a batch problem
+                                              // prefetches its slices into L2
 constexpr long long kClusterWork = 1 << 17;  // nonzeros of Kn + Ā from which a slot launch
                                              // solves its problems on clusters
 
@@ -329,6 +331,10 @@ void fill_batch_devs(osqp_batch* b) {
     };
     d->kn = sched(L.kn_s, o.kn, L.n);
     d->as = sched(L.a_s, o.a, L.m);
+    // a problem whose matrices exceed its share of L2 among the concurrent
+    // problems streams them from DRAM: prefetch its slices
+    const size_t mat_bytes = (size_t)(L.kn_s.npos + L.a_s.npos) * (sizeof(int) + sizeof(T));
+    d->kn.prefetch = d->as.prefetch = mat_bytes > kPrefetchBytes ? 1 : 0;
     dynamic_carve<T>(L, b->arena + L.v_off, d);
   }
 }

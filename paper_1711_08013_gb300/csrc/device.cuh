@@ -53,6 +53,7 @@ struct Sched {
   const int* srow;      // row of local row r of slice s at s·(32/group) + r; −1 = none
   const int4* chunks;   // (row, begin, end, first-chunk-of-row) in positions
   const int* long_rows;
+  int prefetch;         // 1: stream the slices into L2 ahead of use (data not L2-resident)
 };
 
 struct Barrier {
@@ -542,6 +543,18 @@ struct PlainTeam {
 // row in order and the group combines them by a fixed shuffle tree, so a
 // row's result does not depend on where its slice sits.
 // ---------------------------------------------------------------------------
+// Bulk prefetch of one slice's column indices and values into L2 (a slice
+// occupies 32·steps consecutive positions starting at a multiple of 32, so
+// both ranges are 16-byte aligned multiples of 16 bytes).
+template <typename MT>
+__device__ __forceinline__ void prefetch_slice(int2 sl, const int* ci, const MT* va) {
+  if (sl.y <= 0) return;
+  const unsigned bi = 32u * sl.y * (unsigned)sizeof(int);
+  const unsigned bv = 32u * sl.y * (unsigned)sizeof(MT);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ci + sl.x), "r"(bi) : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(va + sl.x), "r"(bv) : "memory");
+}
+
 template <int NV, bool MAXR, typename AT, typename MT, class Team, class G, class R, class C>
 __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* __restrict__ ci,
                                      const MT* __restrict__ va, G gather, R on_row, C on_chunk) {
@@ -552,7 +565,16 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* 
   const int spw = 32 / Gw;
   const int gw = lane / Gw;
   const unsigned gmask = (Gw == 32) ? 0xffffffffu : (((1u << Gw) - 1u) << (gw * Gw));
-  for (int s = tm.warp(); s < S.nslices; s += tm.nwarps()) {
+  // Problems whose data do not stay in L2 (set by the batch for its largest
+  // problems) ask for each warp's slices two steps ahead, so the index/value
+  // stream arrives from DRAM while the dependent gathers run.
+  const int nwt = tm.nwarps();
+  if (S.prefetch && lane == 0)
+    for (int s = tm.warp(); s < S.nslices && s < tm.warp() + 2 * nwt; s += nwt)
+      prefetch_slice(S.slices[s], ci, va);
+  for (int s = tm.warp(); s < S.nslices; s += nwt) {
+    if (S.prefetch && lane == 0 && s + 2 * nwt < S.nslices)
+      prefetch_slice(S.slices[s + 2 * nwt], ci, va);
     const int2 sl = S.slices[s];
     const int row = S.srow[s * spw + gw];
     AT acc[NV];

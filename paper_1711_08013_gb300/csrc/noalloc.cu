@@ -379,6 +379,7 @@ __device__ bool build_sliced(Sched& S, const NaSched& B, NaPtrs<T>& sp, int nrow
       S.srow = B.srow;
       S.chunks = B.chunks;
       S.long_rows = B.long_rows;
+      S.prefetch = 0;
     }
   }
   __syncthreads();

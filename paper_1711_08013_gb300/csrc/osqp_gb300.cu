@@ -245,6 +245,7 @@ void take_sched(Arena& A, const SchedHost& h, int nrows, Sched& S) {
   S.srow = A.take<int>(h.srow.size());
   S.chunks = A.take<int4>(h.chunks.size());
   S.long_rows = A.take<int>(h.long_rows.size());
+  S.prefetch = 0;  // one problem's data stay in L2
 }
 
 template <typename T>
