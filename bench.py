@@ -146,8 +146,9 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------
 # algorithmic bytes of one ADMM launch (stages of the ADMM kernel, each array
-# read or written once per stage; matrix values + column indices + row
-# pointers once per SpMV)
+# read or written once per stage; matrix values + column indices once per
+# sparse product, plus one index per row for the row structure; layout
+# padding is not counted)
 # ----------------------------------------------------------------------------
 def admm_bytes(n, m, nnz_kn, nnz_a, sv, K, J, C):
     d = 8
@@ -212,8 +213,54 @@ def param_oracle(name, k, budget_s=15.0):
     return done, time.perf_counter() - t0, iters
 
 
+def _reference_line(args, workload, value, steps, dt, iters, sample, cores):
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+        "warmup": 0, "ms_per_step": 1e3 * dt / max(1, steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference", "config": {"workload": WORKLOADS[workload][1], "precision": "fp64",
+                                         "eps": 1e-3},
+        "admm_iter_per_s": iters / dt if iters is not None else None,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
+        return 0
+    if args.workload == "mpc_batch":
+        # the oracle on a bounded sample of the batch, one problem per process
+        count = int(os.environ.get("OSQP_BATCH_COUNT", "4096"))
+        cb = batch_cpu_baseline(pb.mpc_batch(count, seed=3000))
+        print(json.dumps(_reference_line(args, "mpc_batch", cb["value"], 1, 1.0 / cb["value"],
+                                         None, cb["sample"], cb["cores"])), flush=True)
+        return 0
+    if args.workload == "serve":
+        # the oracle solving a bounded sample of the request stream (each
+        # request's perturbed QP, warm-started from its problem's previous
+        # solution as the server does), single thread
+        from oracle import oracle as O
+        from paper_1711_08013_gb300.serve import poisson_requests
+        qps = serve_pool(args.nmax, seed=4000)
+        reqs = poisson_requests(qps, args.rate, args.duration, seed=100)
+        last = {}
+        t0 = time.perf_counter()
+        done = iters = 0
+        for r in reqs:
+            q = pb._finish("req", qps[r.pid].P, r.q, qps[r.pid].A, r.l, r.u)
+            x0, y0 = last.get(r.pid, (None, None))
+            res = O.solve(q, x0=x0, y0=y0)
+            last[r.pid] = (res.x, res.y)
+            done += 1
+            iters += res.iter
+            if time.perf_counter() - t0 > 20.0:
+                break
+        dt = time.perf_counter() - t0
+        print(json.dumps(_reference_line(args, "serve", done / dt, done, dt, iters,
+                                         f"first {done} requests of the stream, warm-started, "
+                                         f"single thread, {dt:.1f} s", 1)), flush=True)
         return 0
     if args.workload in PARAM_LEN:
         k = args.seq_len or PARAM_LEN[args.workload]

@@ -134,7 +134,7 @@ void osqp_set_default_settings(osqp_settings* s);
 /* Text for an OSQP_ERR_* code or an OSQP_* status (static storage). */
 const char* osqp_error_message(int32_t code);
 
-/* §1.1 problem statement and §7 CSC input.  Validates, builds the CSR
+/* §1.1 problem statement and §7 CSC input.  Validates, builds the sparse
  * structure of [P̄ Āᵀ] and Ā, allocates all device memory, copies the data
  * and runs Ruiz scaling, the ρ vector and the Jacobi diagonal on the device.
  * stream: a cudaStream_t or NULL.  On success *out owns the solver. */

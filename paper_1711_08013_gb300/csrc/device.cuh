@@ -1,21 +1,24 @@
 // Device code of the OSQP ADMM hot path for sm_103a.
 //
 // One implementation of every stage, templated on a "team" that executes it:
-//   GridTeam  — all CTAs of a cooperative launch, one persistent CTA per SM
-//               slot, synchronised by a bounded grid barrier;
-//   BlockTeam — one CTA (used for small problems and for the batched kernel,
-//               where every CTA owns one problem at a time).
+//   GridTeam    — all CTAs of a cooperative launch, one persistent CTA per SM
+//                 slot, synchronised by a bounded grid barrier;
+//   ClusterTeam — the CTAs of one thread-block cluster, synchronised through
+//                 distributed shared memory (heavy problems of a batch,
+//                 large serving requests, launch = 3);
+//   BlockTeam   — one CTA (small problems and the batched kernel, where every
+//                 CTA owns one problem at a time);
+//   PlainTeam   — an ordinary launch without barriers (warm start).
 // Stages are separated by team-wide barriers; reductions are published by
 // each CTA and combined after the next barrier in a fixed order, so every
 // thread of every CTA derives bit-identical scalars (α, β, residual norms,
 // termination decisions) without a second barrier or a host round trip.
 //
-// Matrices live in CSR form: Kn = [P̄ Āᵀ] (n rows; column c < n addresses P̄,
-// column n + i addresses Āᵀ) and Ā (m rows).  SpMV uses a host-built row
-// schedule: rows up to `long_thresh` nonzeros are handled by a sub-warp of
-// `group` lanes (a power of two picked from the mean row length), longer rows
-// are cut into 256-nonzero chunks that whole warps reduce and add atomically
-// into outputs zeroed in an earlier stage.
+// Matrices: Kn = [P̄ Āᵀ] (n rows; column c < n addresses P̄, column n + i
+// addresses Āᵀ) and Ā (m rows), each in the sliced layout described at
+// Sched: short rows in coalesced 32-lane slices sorted by length, rows
+// longer than `long_thresh` in 256-nonzero chunks that whole warps reduce
+// and add atomically into outputs zeroed in an earlier stage.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>

@@ -1,9 +1,9 @@
 // Host driver and C ABI of the GB300 OSQP library (see include/osqp_gb300.h).
 //
-// Setup (symbolic, host): validate the CSC input, build the CSR structure of
+// Setup (symbolic, host): validate the CSC input, build the structure of
 // Kn = [P̄ Āᵀ] (full symmetric P̄ followed by the column of A that row j of Āᵀ
-// reads) and of Ā, with gather maps from the CSC value arrays, and a row
-// schedule per matrix.  Everything numeric — scattering values, Ruiz
+// reads) and of Ā, lay both out in slices (see Sched in device.cuh) with
+// gather maps from the CSC value arrays.  Everything numeric — scattering values, Ruiz
 // scaling, ρ, the Jacobi diagonal, the ADMM/PCG iteration, residuals,
 // unscaling — runs in the kernels of device.cuh.
 #include <cuda_runtime.h>
