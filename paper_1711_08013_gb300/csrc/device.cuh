@@ -838,11 +838,11 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
   }
   if (!tm.sync()) return false;
   jacobi_rows(tm, d, P.sigma, rho_bar);
+  if (tm.leader()) {  // no residuals on the new data yet: zero = none, −1 = recompute
+    d.sc->rp_last = reset_iterates ? 0.0 : -1.0;
+    d.sc->rd_last = reset_iterates ? 0.0 : -1.0;
+  }
   if (reset_iterates) {
-    if (tm.leader()) {
-      d.sc->rp_last = 0.0;
-      d.sc->rd_last = 0.0;
-    }
     for (int j = tid; j < n; j += nth) {
       d.x[j] = 0.0;
       d.dx[j] = 0.0;
@@ -894,7 +894,13 @@ __device__ bool refresh_stage(Team& tm, const Dev<T>& d, const Params& P, double
   jacobi_rows(tm, d, P.sigma, rho_bar);
   if (!tm.sync()) return false;
   finish_dinv(tm, d);
-  if (tm.leader()) d.sc->rho_bar = rho_bar;
+  if (tm.leader()) {
+    d.sc->rho_bar = rho_bar;
+    // the last check's residuals belong to the old data: recompute them on
+    // the current iterates when the next solve starts
+    d.sc->rp_last = -1.0;
+    d.sc->rd_last = -1.0;
+  }
   return tm.sync();
 }
 
@@ -1167,10 +1173,12 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
 
   int status = kUnsolved, k = 0, pcg_total = 0, rho_updates = 0, checks = 0;
   bool dinv_dirty = false;
-  // PCG tolerance before this solve's first check: the residuals of the last
-  // check on the current iterates (a warm start), else a fraction of ‖b‖
+  // PCG tolerance before this solve's first check: the scaled residuals of
+  // the current iterates (a warm start) — those of the last check, or, when
+  // the data changed since (marked −1), recomputed below — else a fraction
+  // of ‖b‖ (zero iterates)
   double rp_bar = d.sc->rp_last, rd_bar = d.sc->rd_last;
-  bool have_check = rp_bar > 0.0 && rd_bar > 0.0;
+  const bool stale = rp_bar < 0.0 || rd_bar < 0.0;
   double prim_res = NAN, dual_res = NAN, obj = NAN;
   int cur = 0;
 
@@ -1185,7 +1193,44 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   zero_long(tm, d.kn, rbuf(cur));
   zero_long(tm, d.kn, bv);
   zero_long(tm, d.as, tbuf(cur));
+  if (stale) {
+    zero_long(tm, d.kn, d.px);
+    zero_long(tm, d.kn, d.aty);
+    zero_long(tm, d.as, d.ax);
+  }
   if (!tm.sync()) return false;
+  if (stale) {
+    // ‖Āx̄ − z̄‖∞ and ‖P̄x̄ + q̄ + Āᵀȳ‖∞ on the current iterates (§5.1, scaled)
+    spmv<2, false, double, T>(
+        tm, d.kn, kn_ci, kn_v,
+        [&](int col, T v, double* acc) {
+          const double vv = (double)v;
+          if (col < n) acc[0] += vv * x[col];
+          else acc[1] += vv * y[col - n];
+        },
+        [&](int j, double* acc) {
+          d.px[j] = acc[0];
+          d.aty[j] = acc[1];
+        },
+        [&](int j, int, double* acc) {
+          atomicAdd(&d.px[j], acc[0]);
+          atomicAdd(&d.aty[j], acc[1]);
+        });
+    spmv<1, false, double, T>(
+        tm, d.as, a_ci, a_v, [&](int col, T v, double* acc) { acc[0] += (double)v * x[col]; },
+        [&](int i, double* acc) { d.ax[i] = acc[0]; },
+        [&](int i, int, double* acc) { atomicAdd(&d.ax[i], acc[0]); });
+    if (!tm.sync()) return false;
+    double res[2] = {0.0, 0.0};
+    for (int i = tid; i < m; i += nth) res[0] = fmax(res[0], fabs(d.ax[i] - z[i]));
+    for (int j = tid; j < n; j += nth) res[1] = fmax(res[1], fabs(d.px[j] + d.q[j] + d.aty[j]));
+    tm.template publish<2, 3u>(res);
+    if (!tm.sync()) return false;
+    tm.template collect<2, 3u>(res);
+    rp_bar = res[0];
+    rd_bar = res[1];
+  }
+  bool have_check = rp_bar > 0.0 && rd_bar > 0.0;
 
   for (k = 1; k <= P.max_iter; ++k) {
     // --- R: initial PCG residual r⁰ = b − Kx̃ and b = σx − q̄ + Āᵀ(Rz − y),
