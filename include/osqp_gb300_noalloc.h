@@ -38,6 +38,15 @@ extern "C" {
  * longer than 8192 entries; OSQP_ERR_CSC for malformed CSC (checked on the
  * device); the usual codes for bad settings.  The call waits for the stream.
  *
+ * Inside a stream capture (stream is capturing) nothing may wait, so the
+ * call only enqueues the solve and returns OSQP_OK; info must then be NULL
+ * (else OSQP_ERR_ARG).  Every replay of the captured graph reads the input
+ * buffers and writes x, y when it runs, so one graph solves successive
+ * problems of the same n, m and nonzero counts whose values, q, l and u the
+ * caller rewrites in place between replays (a control loop).  The status,
+ * iteration counts and any device-side rejection of a replay (malformed CSC,
+ * too large) are read afterwards with osqp_noalloc_get_info.
+ *
  * The first call made with a given device current looks up the work array's
  * device address (cudaGetSymbolAddress); make that first call before any
  * stream capture.  Every call shares the array and overwrites it: calls whose
@@ -50,6 +59,16 @@ int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_colptr,
                            const double* A_val, int32_t A_nnz, const double* l, const double* u,
                            const osqp_settings* settings, double* x, double* y, osqp_info* info,
                            void* stream);
+
+/* Status of the last solve that ran in the work array (a call of
+ * osqp_solve_noalloc, or a replay of one captured in a CUDA graph) for a
+ * problem with these sizes, nonzero counts and precision (OSQP_PRECISION_*):
+ * fills *info (host) as osqp_solve_noalloc does and returns OSQP_ERR_CSC or
+ * OSQP_ERR_LIMIT when the device rejected that problem.  The sizes locate
+ * the status inside the work array; other sizes read unrelated bytes.
+ * Waits for the stream; OSQP_ERR_ARG inside a stream capture. */
+int32_t osqp_noalloc_get_info(int32_t n, int32_t m, int32_t P_nnz, int32_t A_nnz,
+                              int32_t precision, osqp_info* info, void* stream);
 
 #ifdef __cplusplus
 }

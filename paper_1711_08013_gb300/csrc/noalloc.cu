@@ -579,6 +579,37 @@ int scratch_address(char** out) {
   return OSQP_OK;
 }
 
+// Status of the last solve in the work array for a problem of these sizes:
+// the Scalars sit at a fixed offset of its layout.  Waits for the stream.
+int read_info(const NaInput& in, int precision, char* base, cudaStream_t st, osqp_info* info) {
+  Scalars sc;
+  NaPtrs<double> probe64;
+  NaPtrs<float> probe32;
+  const Scalars* dsc = precision == OSQP_PRECISION_FP64
+                           ? (na_carve<double>(in, base, &probe64), probe64.d.sc)
+                           : (na_carve<float>(in, base, &probe32), probe32.d.sc);
+  if (cudaMemcpyAsync(&sc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return OSQP_ERR_CUDA;
+  if (sc.dev_error == kNaBadCsc) return OSQP_ERR_CSC;
+  if (sc.dev_error == kNaLongRow || sc.dev_error == kNaNoRoom) return OSQP_ERR_LIMIT;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = sc.status;
+    info->iter = sc.iter;
+    info->pcg_iters = sc.pcg_iters;
+    info->rho_updates = sc.rho_updates;
+    info->ruiz_passes = sc.ruiz_passes;
+    info->launch = 1;
+    info->obj_val = sc.obj;
+    info->prim_res = sc.prim_res;
+    info->dual_res = sc.dual_res;
+    info->rho_estimate = sc.rho_bar;
+    info->polished = sc.polished;
+  }
+  return OSQP_OK;
+}
+
 }  // namespace
 
 extern "C" int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_colptr,
@@ -611,6 +642,13 @@ extern "C" int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_col
                           : na_carve<float>(in, nullptr, nullptr) + sliced_bytes<float>(nkn_min) +
                                 sliced_bytes<float>(na_min) + 512;
   if (need > kNoallocScratchBytes) return OSQP_ERR_LIMIT;
+  cudaStream_t st = (cudaStream_t)stream;
+  // Inside a stream capture nothing may wait: the call only enqueues the
+  // solve, and osqp_noalloc_get_info reads its status after a replay.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return OSQP_ERR_CUDA;
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  if (capturing && info) return OSQP_ERR_ARG;
   char* base = nullptr;
   int rc = scratch_address(&base);
   if (rc) return rc;
@@ -638,37 +676,29 @@ extern "C" int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_col
   P.polish = s.polish;
   P.polish_refine = s.polish_refine_iter;
   P.delta = s.delta;
-  cudaStream_t st = (cudaStream_t)stream;
   if (s.precision == OSQP_PRECISION_FP64)
     k_noalloc<double><<<1, kThreads, 0, st>>>(in, P, s.rho, base);
   else
     k_noalloc<float><<<1, kThreads, 0, st>>>(in, P, s.rho, base);
   if (cudaGetLastError() != cudaSuccess) return OSQP_ERR_CUDA;
-  // Scalars sit at a fixed offset of the layout: read them back.
-  Scalars sc;
-  NaPtrs<double> probe64;
-  NaPtrs<float> probe32;
-  const Scalars* dsc = s.precision == OSQP_PRECISION_FP64
-                           ? (na_carve<double>(in, base, &probe64), probe64.d.sc)
-                           : (na_carve<float>(in, base, &probe32), probe32.d.sc);
-  if (cudaMemcpyAsync(&sc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return OSQP_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return OSQP_ERR_CUDA;
-  if (sc.dev_error == kNaBadCsc) return OSQP_ERR_CSC;
-  if (sc.dev_error == kNaLongRow || sc.dev_error == kNaNoRoom) return OSQP_ERR_LIMIT;
-  if (info) {
-    std::memset(info, 0, sizeof(*info));
-    info->status = sc.status;
-    info->iter = sc.iter;
-    info->pcg_iters = sc.pcg_iters;
-    info->rho_updates = sc.rho_updates;
-    info->ruiz_passes = sc.ruiz_passes;
-    info->launch = 1;
-    info->obj_val = sc.obj;
-    info->prim_res = sc.prim_res;
-    info->dual_res = sc.dual_res;
-    info->rho_estimate = sc.rho_bar;
-    info->polished = sc.polished;
-  }
-  return OSQP_OK;
+  if (capturing) return OSQP_OK;
+  return read_info(in, s.precision, base, st, info);
+}
+
+extern "C" int32_t osqp_noalloc_get_info(int32_t n, int32_t m, int32_t P_nnz, int32_t A_nnz,
+                                         int32_t precision, osqp_info* info, void* stream) {
+  if (!info) return OSQP_ERR_ARG;
+  if (n < 1 || m < 0 || P_nnz < 0 || A_nnz < 0) return OSQP_ERR_DIMS;
+  if (precision != OSQP_PRECISION_FP64 && precision != OSQP_PRECISION_FP32_MIXED)
+    return OSQP_ERR_SETTINGS;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return OSQP_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return OSQP_ERR_ARG;
+  char* base = nullptr;
+  int rc = scratch_address(&base);
+  if (rc) return rc;
+  NaInput in{n, m, P_nnz, A_nnz, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+             nullptr, nullptr, nullptr, nullptr};
+  return read_info(in, precision, base, st, info);
 }

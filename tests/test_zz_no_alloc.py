@@ -5,7 +5,8 @@ device memory, and real-time loops that forbid cudaMalloc/cudaFree after
 start-up cannot use osqp_setup, which allocates the solver's device memory.
 osqp_solve_noalloc solves one small QP with every work array inside a fixed,
 statically allocated device buffer.  These tests call it through the C ABI
-and check it against the allocating entry points on two calls in a row.
+and check it against the allocating entry points on two calls in a row, and
+replay it from a CUDA graph on inputs rewritten between replays.
 """
 import ctypes as C
 
@@ -98,3 +99,65 @@ def test_noalloc_matches_allocating_entry_point_twice(name, make, kw):
         assert _rel(xg, ref.x) <= 1e-8, (name, call, _rel(xg, ref.x))
         assert _rel(yg, ref.y) <= 1e-8, (name, call, _rel(yg, ref.y))
         assert abs(info.obj_val - ref.obj_val) <= 1e-8 * max(1.0, abs(ref.obj_val))
+
+
+def get_info_fn():
+    f = B.lib().osqp_noalloc_get_info
+    f.restype = C.c_int32
+    f.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(B.osqp_info), _P]
+    return f
+
+
+def test_noalloc_get_info_rejects_bad_arguments():
+    """Argument checks of the status read-back run on the host before any
+    device call."""
+    f = get_info_fn()
+    info = B.osqp_info()
+    assert f(10, 5, 3, 4, B.FP64, None, None) == B.OSQP_ERR_ARG
+    assert f(0, 5, 3, 4, B.FP64, C.byref(info), None) == B.OSQP_ERR_DIMS
+    assert f(10, -1, 3, 4, B.FP64, C.byref(info), None) == B.OSQP_ERR_DIMS
+    assert f(10, 5, 3, 4, 7, C.byref(info), None) == B.OSQP_ERR_SETTINGS
+
+
+@pytest.mark.gpu
+def test_noalloc_captured_in_cuda_graph_replays_a_control_loop():
+    """Captured once in a CUDA graph, the solve replays on inputs rewritten in
+    place between replays (q, l and u perturbed as a receding-horizon loop
+    does): each replay equals an uncaptured call on the same buffers, and
+    osqp_noalloc_get_info reports the replay's status and iterations."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    qp = pb.mpc(6, 8, seed=23)
+    d = _device_inputs(torch, qp)
+    x = torch.empty(qp.n, dtype=torch.float64, device="cuda")
+    y = torch.empty(qp.m, dtype=torch.float64, device="cuda")
+    st = B.osqp_set_default_settings(launch=1)
+    f, gi = noalloc_fn(), get_info_fn()
+    rc, _, _, _ = _call(torch, f, qp, d, st, x, y)  # first call: before any capture
+    assert rc == B.OSQP_OK
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        rc = f(qp.n, qp.m, d["Pp"].data_ptr(), d["Pi"].data_ptr(), d["Px"].data_ptr(), qp.P.nnz,
+               d["q"].data_ptr(), d["Ap"].data_ptr(), d["Ai"].data_ptr(), d["Ax"].data_ptr(),
+               qp.A.nnz, d["l"].data_ptr(), d["u"].data_ptr(), C.byref(st), x.data_ptr(),
+               y.data_ptr(), None, stream.cuda_stream)
+    assert rc == B.OSQP_OK
+    rng = np.random.default_rng(5)
+    for step in range(3):
+        q2, l2, u2 = pb.perturb_vectors(rng, qp)
+        for key, v in (("q", q2), ("l", l2), ("u", u2)):
+            d[key].copy_(torch.from_numpy(np.ascontiguousarray(v)))
+        x.fill_(float("nan"))
+        y.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        xg, yg = x.cpu().numpy().copy(), y.cpu().numpy().copy()
+        info = B.osqp_info()
+        assert gi(qp.n, qp.m, qp.P.nnz, qp.A.nnz, B.FP64, C.byref(info), None) == B.OSQP_OK
+        rc, ref, xr, yr = _call(torch, f, qp, d, st, x, y)
+        assert rc == B.OSQP_OK and ref.status == B.SOLVED
+        assert info.status == ref.status and info.iter == ref.iter, (step, info.iter, ref.iter)
+        assert _rel(xg, xr) <= 1e-12 and _rel(yg, yr) <= 1e-12, step
