@@ -233,7 +233,7 @@ def run_reference(args, ws, rank):
     if args.workload == "mpc_batch":
         # the oracle on a bounded sample of the batch, one problem per process
         count = int(os.environ.get("OSQP_BATCH_COUNT", "4096"))
-        cb = batch_cpu_baseline(pb.mpc_batch(count, seed=3000))
+        cb, _, _ = batch_cpu_baseline(pb.mpc_batch(count, seed=3000))
         print(json.dumps(_reference_line(args, "mpc_batch", cb["value"], 1, 1.0 / cb["value"],
                                          None, cb["sample"], cb["cores"])), flush=True)
         return 0
@@ -305,20 +305,38 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def result_error(qp, x, y, obj, ox, oobj, eps=1e-3):
+    """A GPU result against the oracle's solution of the same QP at the same
+    ε (objective and x), with the result's own unscaled residuals of §3.4
+    beside their tolerances, all computed on the host in FP64."""
+    P = qp.P_full()
+    Ax, Px, Aty = qp.A @ x, P @ x, qp.A.T @ y
+    viol = np.maximum(Ax - qp.u, 0.0) + np.minimum(Ax - qp.l, 0.0)
+    z = np.clip(Ax, qp.l, qp.u)
+    amax = lambda v: float(np.max(np.abs(v), initial=0.0))
+    return {"obj_rel": abs(obj - oobj) / max(1.0, abs(oobj)),
+            "x_rel": amax(x - ox) / max(1.0, amax(ox)),
+            "prim_res": amax(viol), "eps_prim": eps + eps * max(amax(Ax), amax(z)),
+            "dual_res": amax(Px + qp.q + Aty),
+            "eps_dual": eps + eps * max(amax(Px), amax(Aty), amax(qp.q))}
+
+
 def cpu_baseline(args, qp):
+    """The oracle timed on the same instance; also returns its last solution
+    for the error statement of the GPU result."""
     from oracle import oracle as O
     O.solve(qp)
     t0 = time.perf_counter()
     k = 0
     while True:
-        O.solve(qp)
+        r = O.solve(qp)
         k += 1
         if time.perf_counter() - t0 > 10.0 or k >= 200:
             break
     dt = time.perf_counter() - t0
     return {"value": k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{k} full solves (setup + ADMM) of the same workload instance, "
-                      f"{dt:.1f} s, single thread"}
+                      f"{dt:.1f} s, single thread"}, r
 
 
 def batch_main(args, ws, rank, local):
@@ -423,7 +441,8 @@ def batch_main(args, ws, rank, local):
     }
     bs.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = batch_cpu_baseline(qps)
+        line["cpu_baseline"], idx, out = batch_cpu_baseline(qps)
+        line["oracle_error"] = batch_error(qps, last, idx, out)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -434,7 +453,7 @@ def batch_main(args, ws, rank, local):
 def _oracle_solve_one(qp):
     from oracle import oracle as O
     r = O.solve(qp)
-    return r.status
+    return r.status, r.x, r.obj_val
 
 
 def batch_cpu_baseline(qps, sample=256):
@@ -443,17 +462,34 @@ def batch_cpu_baseline(qps, sample=256):
     import multiprocessing as mp
     from oracle import oracle as O
     O.build()
-    sub = qps[:: max(1, len(qps) // sample)][:sample]
+    idx = list(range(0, len(qps), max(1, len(qps) // sample)))[:sample]
+    sub = [qps[i] for i in idx]
     cores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
         pool.map(_oracle_solve_one, sub[:cores])  # warm the workers
         t0 = time.perf_counter()
-        pool.map(_oracle_solve_one, sub, chunksize=1)
+        out = pool.map(_oracle_solve_one, sub, chunksize=1)
         dt = time.perf_counter() - t0
     return {"value": len(sub) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(sub)} of the {len(qps)} batch problems, one per process on "
-                      f"{cores} cores, {dt:.1f} s"}
+                      f"{cores} cores, {dt:.1f} s"}, idx, out
+
+
+def batch_error(qps, results, idx, out):
+    """Error statement of the batch results on the oracle's sample: the worst
+    and median objective and x differences, and the worst residual as a
+    fraction of its tolerance."""
+    errs = [result_error(qps[i], results[i].x, results[i].y, results[i].obj_val, ox, oobj)
+            for i, (_, ox, oobj) in zip(idx, out)]
+    med = lambda v: float(statistics.median(v))
+    return {"problems": len(errs), "reference": "oracle (FP64, direct method) at the same eps",
+            "obj_rel_max": max(e["obj_rel"] for e in errs),
+            "obj_rel_median": med([e["obj_rel"] for e in errs]),
+            "x_rel_max": max(e["x_rel"] for e in errs),
+            "x_rel_median": med([e["x_rel"] for e in errs]),
+            "prim_res_over_eps_max": max(e["prim_res"] / e["eps_prim"] for e in errs),
+            "dual_res_over_eps_max": max(e["dual_res"] / e["eps_dual"] for e in errs)}
 
 
 def serve_pool(nmax, seed=4000):
@@ -758,7 +794,10 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, qp)
+        line["cpu_baseline"], o = cpu_baseline(args, qp)
+        g = infos[-1]
+        line["oracle_error"] = dict(result_error(qp, g.x, g.y, g.obj_val, o.x, o.obj_val),
+                                    reference="oracle (FP64, direct method) at the same eps")
     s.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
