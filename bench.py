@@ -151,6 +151,18 @@ class ClockSampler:
 # padding is not counted)
 # ----------------------------------------------------------------------------
 def admm_bytes(n, m, nnz_kn, nnz_a, sv, K, J, C):
+    """Algorithmic bytes of one solve of K ADMM iterations, J PCG iterations
+    and C checks: every matrix pass streams its values (sv bytes each), int32
+    column indices and int32 row pointers once, and every vector a stage
+    touches is read or written once (d = 8 bytes for FP64 vectors, sv for
+    working-precision ones); gathers are counted once per stage, as if the
+    vector were cached.  Stages: R (Kn pass, first PCG residual and b), A0
+    (first Ā pass, M⁻¹r), U (Algorithm 1 steps 5-7); per PCG iteration the Kn
+    pass B (w = Ku) and the elementwise updates and inner products Cc, and
+    the Ā pass A for every PCG iteration after the first of its ADMM
+    iteration; per check K1 (the FP64 products) and K2 (the norms).  A PCG
+    iteration thus streams (nnz(P) + 2·nnz(A))·(sv + 4) matrix bytes, with
+    nnz_kn = nnz(P full) + nnz(A)."""
     d = 8
     kn = nnz_kn * (sv + 4) + 4 * (n + 1)
     am = nnz_a * (sv + 4) + 4 * (m + 1)
