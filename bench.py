@@ -624,7 +624,7 @@ def param_main(args, ws, rank, local):
         "ws_ms_per_qp": 1e3 * ws_s, "cold_ms_per_qp": 1e3 * cold_s, "cold_qps": len(cold),
         "ws_iter_per_qp": it_ws, "cold_iter_per_qp": it_cold,
         "time_improvement": cold_s / ws_s, "iter_improvement": it_cold / it_ws,
-        "paper_context": dict(PARAM_PAPER[args.workload], hardware="CPU (OSQP direct method)"),
+        "paper_context": dict(PARAM_PAPER[args.workload], hardware="MIT SuperCloud node with 16 Intel Xeon E5-2650 cores; OSQP with the single-threaded QDLDL direct solver (paper, Sec. 8)"),
         "roofline": {"bound": "hbm", "kernel": kernel, "achieved": algo / dev_s / 1e9,
                      "peak": peak, "unit": "GB/s", "frac": algo / dev_s / 1e9 / peak,
                      "traffic": None, "algorithmic_bytes_per_launch": algo / len(steps)},
