@@ -295,6 +295,26 @@ int32_t osqp_batch_cleanup(osqp_batch* b);
  * and frees a few bytes of device memory; synchronises the device. */
 int32_t osqp_diag_barrier_timeout(double timeout_s);
 
+/* Diagnostic of the sliced sparse layout that osqp_setup builds for every
+ * matrix (host only: no device work).  Input: the CSR row pointers of an
+ * nrows-row matrix (rowptr[0] = 0, non-decreasing; nnz = rowptr[nrows]) and
+ * the number of warps that run its products (16 for one CTA, 16 per CTA of
+ * a grid).  Rows of at most max(256, 8·mean) nonzeros are sorted by
+ * decreasing length (stable in the row index) into slices of 32/G rows,
+ * G = stats[0] lanes per row; step t of a slice holds one nonzero per lane
+ * at first + 32t + lane, a row's j-th nonzero on lane G·(its place in the
+ * slice) + j mod G at step ⌊j/G⌋.  Longer rows follow the slices in CSR
+ * order and are split into chunks of 256 positions.
+ * Outputs (host, caller-owned): pos[k] (nnz entries, may be NULL) = the
+ * position of CSR entry k; chunks (4 per chunk, may be NULL) = row, first
+ * position, end position, and 1 for the first chunk of its row else 0; stats[6] =
+ * {G, long-row threshold, slices, positions including padding, long rows,
+ * chunks}.  Returns OSQP_ERR_ARG for a negative nrows, NULL rowptr or stats,
+ * nwarps < 1; OSQP_ERR_CSC for row pointers that do not start at 0 or
+ * decrease. */
+int32_t osqp_diag_sliced_layout(int32_t nrows, const int32_t* rowptr, int64_t nwarps,
+                                int32_t* pos, int32_t* chunks, int32_t* stats);
+
 #ifdef __cplusplus
 }
 #endif

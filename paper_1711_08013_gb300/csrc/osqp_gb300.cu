@@ -935,6 +935,31 @@ int32_t osqp_diag_barrier_timeout(double timeout_s) {
   return rc;
 }
 
+int32_t osqp_diag_sliced_layout(int32_t nrows, const int32_t* rowptr, int64_t nwarps,
+                                int32_t* pos, int32_t* chunks, int32_t* stats) {
+  if (nrows < 0 || !rowptr || nwarps < 1 || !stats) return OSQP_ERR_ARG;
+  if (rowptr[0] != 0) return OSQP_ERR_CSC;
+  for (int32_t r = 0; r < nrows; ++r)
+    if (rowptr[r + 1] < rowptr[r]) return OSQP_ERR_CSC;
+  const std::vector<int> rp(rowptr, rowptr + nrows + 1);
+  const host::SchedHost S = host::make_sched(rp, nwarps);
+  stats[0] = S.group;
+  stats[1] = S.long_thresh;
+  stats[2] = (int32_t)S.slices.size();
+  stats[3] = S.npos;
+  stats[4] = (int32_t)S.long_rows.size();
+  stats[5] = (int32_t)S.chunks.size();
+  if (pos) std::copy(S.pos.begin(), S.pos.end(), pos);
+  if (chunks)
+    for (size_t c = 0; c < S.chunks.size(); ++c) {
+      chunks[4 * c + 0] = S.chunks[c].x;
+      chunks[4 * c + 1] = S.chunks[c].y;
+      chunks[4 * c + 2] = S.chunks[c].z;
+      chunks[4 * c + 3] = S.chunks[c].w;
+    }
+  return OSQP_OK;
+}
+
 int32_t osqp_cleanup(osqp_solver* s) {
   if (!s) return OSQP_ERR_ARG;
   int rc = OSQP_OK;
