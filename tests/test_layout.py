@@ -128,3 +128,12 @@ def test_rejects_bad_row_pointers(layout):
     ok = np.array([0, 1], dtype=np.int32)
     assert f(1, ok.ctypes.data, 0, None, None, stats.ctypes.data) == B.OSQP_ERR_ARG
     assert f(1, ok.ctypes.data, 16, None, None, None) == B.OSQP_ERR_ARG
+
+
+def test_degenerate_matrices(layout):
+    """No rows, and rows without nonzeros: no positions, no long rows; empty
+    rows still take their place in a slice (their product writes a zero)."""
+    _, pos, chunks, st = layout(np.zeros(0, dtype=np.int64), 16)
+    assert list(st[2:]) == [0, 0, 0, 0] and pos.size == 0 and chunks.size == 0
+    _, pos, chunks, st = layout(np.zeros(40, dtype=np.int64), 16)
+    assert st[0] == 1 and st[2] == (40 + 31) // 32 and st[3] == 0 and st[4] == 0
