@@ -78,6 +78,12 @@ class Server:
         status stays 0) and the run ends when the work in flight finishes —
         the way an overloaded server is measured."""
         reqs = sorted(requests, key=lambda r: r.t_arrival)
+        for r in reqs:  # the library reads n (q) and m (l, u) values per request
+            qp = self.qps[r.pid]
+            for name, v, size in (("q", r.q, qp.n), ("l", r.l, qp.m), ("u", r.u, qp.m)):
+                if v is not None and np.size(v) != size:
+                    raise ValueError(f"request for problem {r.pid}: {name} has {np.size(v)} "
+                                     f"entries, expected {size}")
         pending = collections.deque()
         free = list(range(self.slots))[::-1]
         busy = {}

@@ -27,11 +27,20 @@ class Result:
     polished: int = 0
 
 
+def _sized(name, v, size):
+    """The C ABI reads exactly `size` values behind each pointer: refuse
+    arrays of another length before they reach it."""
+    if v is not None and np.size(v) != size:
+        raise ValueError(f"{name} has {np.size(v)} entries, expected {size}")
+    return v
+
+
 class Solver:
     """``Solver(qp, **settings)`` with ``qp`` exposing P (upper CSC), q, A, l, u."""
 
     def __init__(self, qp, stream: int | None = None, **settings):
         self.n, self.m = qp.P.shape[0], qp.A.shape[0]
+        self.nnz_p, self.nnz_a = qp.P.nnz, qp.A.nnz
         self.settings = B.osqp_set_default_settings(**settings)
         self.handle = B.osqp_setup(qp.P, qp.q, qp.A, qp.l, qp.u, self.settings, stream)
 
@@ -49,16 +58,18 @@ class Solver:
         return B.osqp_get_certificate(self.handle, self.n, self.m)
 
     def update_vectors(self, q=None, l=None, u=None):
-        B.osqp_update_vectors(self.handle, q, l, u)
+        B.osqp_update_vectors(self.handle, _sized("q", q, self.n), _sized("l", l, self.m),
+                              _sized("u", u, self.m))
 
     def update_matrices(self, P_val=None, A_val=None):
-        B.osqp_update_matrices(self.handle, P_val, A_val)
+        B.osqp_update_matrices(self.handle, _sized("P_val", P_val, self.nnz_p),
+                               _sized("A_val", A_val, self.nnz_a))
 
     def update_rho(self, rho_bar: float):
         B.osqp_update_rho(self.handle, rho_bar)
 
     def warm_start(self, x=None, y=None):
-        B.osqp_warm_start(self.handle, x, y)
+        B.osqp_warm_start(self.handle, _sized("x", x, self.n), _sized("y", y, self.m))
 
     def close(self):
         if self.handle:
@@ -96,7 +107,9 @@ class BatchSolver:
         B.osqp_batch_reset(self.handle)
 
     def update_vectors(self, i, q=None, l=None, u=None):
-        B.osqp_batch_update_vectors(self.handle, i, q, l, u)
+        n, m = self.sizes[i]
+        B.osqp_batch_update_vectors(self.handle, i, _sized("q", q, n), _sized("l", l, m),
+                                    _sized("u", u, m))
 
     def result(self, i) -> Result:
         n, m = self.sizes[i]

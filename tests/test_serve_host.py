@@ -40,7 +40,7 @@ class FakeBackend:
         new = sum(self.fp[p] for p in pids)
         old = sum(self.fp[p] for p in busy)
         assert old + new <= self.budget or (len(pids) == 1 and old == 0)
-        assert len(qs) == len(ls) == len(us) == len(pids)
+        assert qs is None or len(qs) == len(pids)
         self.running[slot] = [list(pids), 0]
         self.launched.append((slot, list(pids)))
 
@@ -91,8 +91,7 @@ def fake_clock(step):
 
 def requests(rng, nprob, count, rate):
     t = np.cumsum(rng.exponential(1.0 / rate, count))
-    return [serve.Request(int(rng.integers(nprob)), float(ti), np.zeros(1), np.zeros(1),
-                          np.zeros(1)) for ti in t]
+    return [serve.Request(int(rng.integers(nprob)), float(ti)) for ti in t]
 
 
 @pytest.mark.parametrize("slots,budget,max_batch,large", [
@@ -121,7 +120,7 @@ def test_admission_invariants_and_every_request_served(monkeypatch, slots, budge
 
 def test_requests_for_one_problem_are_served_in_arrival_order(monkeypatch):
     srv, be, _ = make_server(monkeypatch, 3, 4, None, (), None, 3, seed=1)
-    reqs = [serve.Request(1, 0.001 * k, np.zeros(1), np.zeros(1), np.zeros(1)) for k in range(6)]
+    reqs = [serve.Request(1, 0.001 * k) for k in range(6)]
     srv.run(reqs, clock=fake_clock(1e-3))
     assert [pids for _, pids in be.launched] == [[1]] * 6
     launch_times = [r.t_launch for r in reqs]
@@ -140,3 +139,12 @@ def test_deadline_drops_unlaunched_requests(monkeypatch):
     assert len(be.launched) == len(served)
     assert all(r.t_launch <= 0.2 + 1e-9 for r in served)
     assert all(r.status == 0 and r.t_launch != r.t_launch for r in reqs if r.t_done != r.t_done)
+
+
+def test_requests_with_wrong_vector_lengths_are_refused(monkeypatch):
+    srv, be, qps = make_server(monkeypatch, 3, 2, None, (), None, 3, seed=4)
+    good = serve.Request(0, 0.0, np.zeros(qps[0].n), np.zeros(qps[0].m), np.zeros(qps[0].m))
+    bad = serve.Request(2, 0.001, np.zeros(qps[2].n + 1), None, None)
+    with pytest.raises(ValueError, match="q has"):
+        srv.run([good, bad], clock=fake_clock(1e-3))
+    assert be.launched == []          # refused before anything ran
