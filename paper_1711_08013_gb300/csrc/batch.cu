@@ -327,7 +327,8 @@ void fill_batch_devs(osqp_batch* b) {
                    (const int2*)(sb + so.sl),
                    (const int*)(sb + so.sr),
                    (const int4*)(sb + so.ch),
-                   (const int*)(sb + so.lr)};
+                   (const int*)(sb + so.lr),
+                   0};  // prefetch: set below from the matrix bytes
     };
     d->kn = sched(L.kn_s, o.kn, L.n);
     d->as = sched(L.a_s, o.a, L.m);
