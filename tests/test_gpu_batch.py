@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover - CPU container
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from paper_1711_08013_gb300.solver import BatchSolver, Solver  # noqa: E402
+from paper_1711_08013_gb300.solver import BatchSolver  # noqa: E402
 
 HIGH_ORACLE = dict(eps_abs=1e-9, eps_rel=1e-9, max_iter=400000, check_interval=10)
 
