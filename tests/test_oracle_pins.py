@@ -307,6 +307,34 @@ def test_ruiz_equilibrates_rows_and_columns(oracle_mod):
     assert s["c"] == 1.0
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_ruiz_cost_normalised_after_last_pass(oracle_mod, seed):
+    """Alg. 2 ends each pass by scaling the cost with γ = 1/max(mean_j
+    ‖P̄_:j‖∞, ‖q̄‖∞), so after the last pass that maximum is 1 (the data
+    here keep both norms inside the clamp of reading R3)."""
+    qp = pb.random_qp(30, seed=40 + seed)
+    Pf = qp.P_full()
+    s = oracle_mod.ruiz(Pf, qp.q, qp.A, qp.l, qp.u, scaling_iters=7, eps_equil=0.0)
+    Pbar = sp.csc_matrix((s["P_x"], Pf.indices, Pf.indptr), shape=Pf.shape)
+    mean_col = float(np.mean(abs(Pbar).max(axis=0).toarray()))
+    assert max(mean_col, float(np.max(np.abs(s["q"])))) == pytest.approx(1.0, rel=1e-12)
+    assert s["passes"] == 7
+
+
+def test_ruiz_cost_scale_bounded_without_linear_cost(oracle_mod):
+    """Reading R3: with q = 0 the vanishing ‖q̄‖∞ counts as 1 in the max, so
+    γ ≤ 1 every pass and c stays at most 1 however many passes run (taken
+    literally, 1/mean_j ‖P̄_:j‖∞ with mostly-zero columns of P̄ would grow c
+    pass after pass)."""
+    qp = pb.mpc(6, 10, seed=3)
+    assert not np.any(qp.q)
+    Pf = qp.P_full()
+    cs = [oracle_mod.ruiz(Pf, qp.q, qp.A, qp.l, qp.u, scaling_iters=k, eps_equil=0.0)["c"]
+          for k in (5, 10, 30)]
+    assert all(0.0 < c <= 1.0 for c in cs)
+    assert cs[2] >= 0.5 * cs[1]
+
+
 def test_scaling_does_not_change_solution(oracle_mod):
     qp = pb.random_qp(25, seed=11)
     a = oracle_mod.solve(qp, scaling_iters=0, **HIGH)
