@@ -216,6 +216,111 @@ def test_dual_infeasibility_certificate(oracle_mod, seed):
     assert dual_cert_ok(qp, r.dual_cert, eps=1e-3)
 
 
+# Certificates and reported residuals are unscaled (§5.1): pinned on badly
+# scaled data, where a missing D, E or c changes the answer.
+def _resid(qp, x, y, z):
+    P = qp.P_full()
+    return (float(np.max(np.abs(qp.A @ x - z), initial=0.0)),
+            float(np.max(np.abs(P @ x + qp.q + qp.A.T @ y))))
+
+
+@pytest.mark.parametrize("make", [lambda: pb.random_qp(30, seed=5), lambda: pb.mpc(5, 6, seed=2),
+                                  lambda: pb.lasso(4, seed=3), lambda: pb.portfolio(2, seed=1)])
+def test_reported_residuals_match_returned_point(oracle_mod, make):
+    qp = make()
+    r = oracle_mod.solve(qp)
+    rp, rd = _resid(qp, r.x, r.y, r.z)
+    assert r.prim_res == pytest.approx(rp, rel=1e-9, abs=1e-14)
+    assert r.dual_res == pytest.approx(rd, rel=1e-9, abs=1e-14)
+
+
+def _scaled_rows(qp, seed):
+    rng = np.random.default_rng(seed)
+    f = np.exp(rng.uniform(-3, 3, qp.m))
+    Fm = sp.diags(f)
+    return pb._finish(qp.name + "_rs", qp.P, qp.q, sp.csc_matrix(Fm @ qp.A), qp.l * f, qp.u * f)
+
+
+def _scaled_cols(qp, seed):
+    rng = np.random.default_rng(seed)
+    g = np.exp(rng.uniform(-3, 3, qp.n))
+    G = sp.diags(g)
+    P = sp.csc_matrix(sp.triu(G @ qp.P_full() @ G))
+    return pb._finish(qp.name + "_cs", P, g * qp.q, sp.csc_matrix(qp.A @ G), qp.l, qp.u)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_primal_certificate_on_badly_scaled_rows(oracle_mod, seed):
+    qp = _scaled_rows(pb.primal_infeasible_qp(4, seed=seed), 50 + seed)
+    r = oracle_mod.solve(qp)
+    assert r.status == oracle_mod.PRIMAL_INFEASIBLE
+    assert primal_cert_ok(qp, r.prim_cert, eps=1e-3)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dual_certificate_on_badly_scaled_columns(oracle_mod, seed):
+    qp = _scaled_cols(pb.dual_infeasible_lp(4 + seed, seed=seed), 60 + seed)
+    r = oracle_mod.solve(qp)
+    assert r.status == oracle_mod.DUAL_INFEASIBLE
+    assert dual_cert_ok(qp, r.dual_cert, eps=1e-3)
+
+
+def _coupled_dinf(seed):
+    """min −x₁ − x₂ + q₃x₃ s.t. x₁ − x₂ = 0, x₁ ≥ 0, x₃ ∈ [−1, 1], columns
+    scaled by random factors: unbounded along G⁻¹(1, 1, 0)."""
+    rng = np.random.default_rng(seed)
+    g = np.exp(rng.uniform(-2, 2, 3))
+    A = sp.csc_matrix(np.array([[1.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]]) @ np.diag(g))
+    q = np.array([-1.0, -1.0, rng.uniform(-1, 1)]) * g
+    return pb._finish("dinf_coupled", sp.csc_matrix((3, 3)), q, A,
+                      np.array([0.0, 0.0, -1.0]), np.array([0.0, np.inf, 1.0])), g
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dual_certificate_couples_scaled_columns(oracle_mod, seed):
+    qp, g = _coupled_dinf(seed)
+    r = oracle_mod.solve(qp)
+    assert r.status == oracle_mod.DUAL_INFEASIBLE
+    assert dual_cert_ok(qp, r.dual_cert, eps=1e-3)
+    d = r.dual_cert / np.linalg.norm(r.dual_cert)
+    ref = np.array([1.0 / g[0], 1.0 / g[1], 0.0])
+    assert np.allclose(d, ref / np.linalg.norm(ref), atol=1e-3)
+
+
+def test_primal_certificate_with_one_sided_rows(oracle_mod):
+    rng = np.random.default_rng(4)
+    n = 5
+    rows = [np.eye(1, n, 0).ravel(), np.eye(1, n, 0).ravel()]
+    A = np.vstack(rows + [rng.standard_normal((6, n))])
+    l = np.array([1.0, -np.inf] + [-5.0, -np.inf, -5.0, -np.inf, -5.0, -np.inf])
+    u = np.array([np.inf, 0.0] + [np.inf, 5.0, np.inf, 5.0, np.inf, 5.0])
+    qp = pb._finish("pinf_onesided", sp.eye(n), rng.standard_normal(n), sp.csc_matrix(A), l, u)
+    r = oracle_mod.solve(qp)
+    assert r.status == oracle_mod.PRIMAL_INFEASIBLE
+    assert primal_cert_ok(qp, r.prim_cert, eps=1e-3)
+
+
+def test_primal_infeasibility_with_active_one_sided_rows(oracle_mod):
+    """x₁ ≥ 1 and x₁ ≤ 0 conflict while one-sided rows (x₂ ≥ 1, x₃ ≤ −1,
+    x₄ ≥ 0.5) are held at their finite bounds by the cost.  Their multipliers
+    settle at finite values, so a difference δy on such a row can carry the
+    sign of its infinite side; paired with ±∞ it would make the support
+    function of §3.4 infinite and hide the certificate.  Every instance must
+    be declared primal infeasible with a valid certificate (reading R17)."""
+    for seed in range(30):
+        rng = np.random.default_rng(seed)
+        n = 4
+        A = np.vstack([np.eye(1, n, 0).ravel(), np.eye(1, n, 0).ravel(), np.eye(n)[1:],
+                       rng.standard_normal((2, n))])
+        l = np.array([1.0, -np.inf, 1.0, -np.inf, 0.5, -np.inf, -np.inf])
+        u = np.array([np.inf, 0.0, np.inf, -1.0, np.inf, 3.0, 3.0])
+        q = np.array([0.0, 5.0, -5.0, 5.0]) + 0.3 * rng.standard_normal(n)
+        qp = pb._finish("pinf_active_onesided", sp.eye(n) * 0.1, q, sp.csc_matrix(A), l, u)
+        r = oracle_mod.solve(qp, max_iter=4000)
+        assert r.status == oracle_mod.PRIMAL_INFEASIBLE, (seed, r.status, r.iter)
+        assert primal_cert_ok(qp, r.prim_cert, eps=1e-3), seed
+
+
 def test_feasible_problems_are_not_flagged(oracle_mod):
     for seed in range(10):
         r = oracle_mod.solve(pb.random_qp(20, seed=seed))
