@@ -452,6 +452,18 @@ def test_scaling_does_not_change_solution(oracle_mod):
 # ρ̄ adaptation direction (§5.2): the rule raises ρ̄ when the normalised primal
 # residual dominates and lowers it when the dual one does.
 # ----------------------------------------------------------------------------
+def test_rho_update_gated_by_tolerance_factor(oracle_mod):
+    """Reading R6: a new ρ̄ is applied only when it is more than the
+    tolerance factor away.  ρ̄ stays in [1e-6, 1e6], so no proposal can be
+    1e13 times away (no update ever), while with factor 1 any proposal that
+    differs at all is applied."""
+    qp = pb.random_qp(30, seed=2)
+    never = oracle_mod.solve(qp, adaptive_rho_tolerance=1e13, max_iter=400)
+    always = oracle_mod.solve(qp, adaptive_rho_tolerance=1.0, max_iter=400)
+    assert never.rho_updates == 0 and never.rho_bar == 0.1
+    assert always.rho_updates >= 1 and always.rho_bar != 0.1
+
+
 def test_rho_adaptation_direction(oracle_mod):
     qp = pb.random_qp(30, seed=2)
     lo = oracle_mod.solve(qp, rho=1e-5, max_rho_updates=1)
