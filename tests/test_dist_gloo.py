@@ -32,6 +32,21 @@ def test_lpt_partition_properties():
     assert D.lpt_partition([5.0, 1.0, 1.0], 2) == [[0], [1, 2]]
 
 
+def test_lpt_within_grahams_bound_of_the_optimum():
+    """Graham's bound for longest-processing-time scheduling: the heaviest
+    bin is at most (4/3 − 1/(3m)) times the optimal makespan, the optimum
+    found here by enumerating every assignment of up to 9 items."""
+    import itertools
+    rng = np.random.default_rng(5)
+    for trial in range(40):
+        parts = int(rng.integers(2, 4))
+        w = rng.lognormal(0, 1.0, size=int(rng.integers(parts + 1, 10)))
+        opt = min(max(np.bincount(a, weights=w, minlength=parts))
+                  for a in itertools.product(range(parts), repeat=len(w)))
+        lpt = max(w[b].sum() for b in D.lpt_partition(w, parts))
+        assert lpt <= (4.0 / 3.0 - 1.0 / (3 * parts)) * opt + 1e-12, (trial, lpt, opt)
+
+
 def _worker(rank, world, port, out_dir):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
                       WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
