@@ -58,7 +58,7 @@ PARAM_LEN = {"lasso_path": 100, "mpc_loop": 100, "portfolio_bt": 960}
 # problems scaled by the problems of the launch.  Absent: not captured.
 TRAFFIC = {("lasso", "fp64"): 20.783616e6, ("lasso", "fp32"): 15.043328e6,
            ("random", "fp64"): 0.519936e6}
-TRAFFIC_BATCH_PER_PROBLEM = {"fp32": 100.647058944e9 / 608}
+TRAFFIC_BATCH_PER_PROBLEM = {}
 # Mean time per QP and mean iterations per QP that the paper reports for the
 # same sequences (OSQP direct method on a CPU; context only)
 PARAM_PAPER = {

@@ -60,8 +60,13 @@ class QP:
 
 
 def _csc(M) -> sp.csc_matrix:
+    """CSC with int32 indices, sorted, duplicates summed and stored zeros
+    dropped (block constructions such as the MPC dynamics, a block-sparse
+    Kronecker product minus an identity, store whole blocks with their
+    zeros)."""
     M = sp.csc_matrix(M)
     M.sum_duplicates()
+    M.eliminate_zeros()
     M.sort_indices()
     M.indices = M.indices.astype(np.int32)
     M.indptr = M.indptr.astype(np.int32)
