@@ -110,3 +110,34 @@ def test_config4_serving_pool():
     assert qp.m == 300
     h = pb.huber(6, seed=1)
     assert h.meta["m_data"] == 600
+
+
+def test_svm_workload():
+    """App. A.7 (bench workload svm: 100 features, 10⁴ points): labels +1 on
+    the first half, −1 on the rest; features N(±1/n, 1/n) at 15%; rows
+    t ≥ diag(b)A_d x + 1 and t ≥ 0; P = blockdiag(2I, 0), q = (0, λ1)."""
+    qp = pb.svm(100, seed=7000)
+    n, m = 100, 10000
+    assert (qp.n, qp.m) == (n + m, 2 * m)
+    D = qp.A[:m, :n].toarray()          # diag(b)·A_d
+    assert np.allclose(qp.A[:m, n:].toarray(), -np.eye(m))
+    top, bot = D[: m // 2], -D[m // 2:]  # undo the labels: rows of A_d
+    for half, mean in ((top, 1.0 / n), (bot, -1.0 / n)):
+        vals = half[half != 0]
+        assert 0.145 <= vals.size / half.size <= 0.155
+        assert abs(vals.mean() - mean) < 0.1 / np.sqrt(n)
+        assert abs(vals.std() - 1.0 / np.sqrt(n)) < 0.05 / np.sqrt(n)
+    assert np.all(np.isinf(qp.l[:m])) and np.all(qp.u[:m] == -1)
+    assert np.all(qp.l[m:] == 0) and np.all(np.isinf(qp.u[m:]))
+    assert np.array_equal(qp.P.diagonal()[:n], np.full(n, 2.0)) and qp.P.nnz == n
+    assert np.all(qp.q[:n] == 0) and np.all(qp.q[n:] == 1.0)
+
+
+def test_eq_qp_workload():
+    """App. A.2 (bench workload eqqp, n = 1000): m = n/2 equality rows
+    l = u = b; P = MMᵀ + 1e-2·I with M at 15%."""
+    qp = pb.eq_qp(1000, seed=8000)
+    assert (qp.n, qp.m) == (1000, 500)
+    assert np.array_equal(qp.l, qp.u)
+    assert 0.14 <= qp.A.nnz / (500 * 1000) <= 0.16
+    assert np.linalg.eigvalsh(qp.P_full().toarray()).min() >= 1e-2 - 1e-8
