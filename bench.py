@@ -447,7 +447,9 @@ def batch_main(args, ws, rank, local):
         "e2e": {"value": ws * count * e2e_steps / e2e_dt, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * sum(q.n + 2 * q.m for q in qps),
                 "d2h_bytes_per_step": 8 * sum(q.n + q.m for q in qps)},
-        "gpu_launches": args.steps,
+        # k_batch every step, plus k_batch_cluster when heavy problems went to
+        # clusters (their results report launch 3; the order repeats each step)
+        "gpu_launches": args.steps * (1 + int(any(r.launch == 3 for r in last))),
         "clocks": clocks,
     }
     bs.close()
