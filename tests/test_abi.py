@@ -104,3 +104,29 @@ def test_null_arguments(lib):
     assert lib.osqp_solve(None) == B.OSQP_ERR_ARG
     assert lib.osqp_cleanup(None) == B.OSQP_ERR_ARG
     assert lib.osqp_update_rho(None, C.c_double(1.0)) == B.OSQP_ERR_ARG
+
+
+def _batch_rc(qps, **settings):
+    try:
+        h = B.osqp_batch_setup(qps, B.osqp_set_default_settings(**settings))
+    except B.OsqpError as e:
+        return e.code
+    B.osqp_batch_cleanup(h)
+    return 0
+
+
+def test_batch_setup_validates_every_problem_on_the_host(lib):
+    """osqp_batch_setup checks each problem as osqp_setup does, before any
+    device work: the first invalid problem decides the error code."""
+    good = pb.random_qp(5, 12, seed=1)
+    lgtu = pb._finish("lgtu", good.P, good.q, good.A, good.u + 1.0, good.u)
+    nan_q = pb._finish("nan", good.P, np.where(np.arange(good.n) == 1, np.nan, good.q), good.A,
+                       good.l, good.u)
+    full_p = pb.unconstrained_qp(6, seed=1)
+    full_p.P = sp.csc_matrix(full_p.P_full().toarray())
+    full_p.P.sort_indices()
+    assert _batch_rc([good, lgtu]) == B.OSQP_ERR_LGTU
+    assert _batch_rc([nan_q, good]) == B.OSQP_ERR_NONFINITE
+    assert _batch_rc([good, full_p]) == B.OSQP_ERR_CSC
+    assert _batch_rc([good], alpha=2.0) == B.OSQP_ERR_SETTINGS
+    assert _batch_rc([]) == B.OSQP_ERR_ARG
