@@ -1,15 +1,22 @@
 #!/usr/bin/env python3
-"""Benchmark: QP solves/s of the GB300 OSQP path on the Lasso workload.
+"""Benchmark: QP solves/s of the GB300 OSQP path, batched vs plain.
 
-One step = one whole solve of one QP: load the raw problem data (already in
-HBM) into the solver, Ruiz scaling, ρ vector and Jacobi diagonal, the ADMM
-iterations with PCG linear solves to ε_abs = ε_rel = 1e-3, unscaling.  The
-timed region covers K steps on the device (CUDA events on the solver's
-stream); L2 is flushed by a 256 MB write between steps, outside the events.
+Default workload: 4096 ragged MPC QPs (App. A.3 generator) solved cold in
+one persistent batched launch, FP32-mixed, ε_abs = ε_rel = 1e-3.  One step
+= one cold solve of every problem of the batch (Ruiz scaling, ρ vector and
+Jacobi diagonal, the ADMM iterations with PCG linear solves, termination,
+unscaling), timed on the device (CUDA events on the solver's stream); the
+batch's data (GBs) exceed L2, so no flush is needed.  The same line carries
+the plain single-problem FP64 form (the 20000 × 200 Lasso QP, one solve per
+step, L2 flushed between steps) under "plain", so batched and plain come
+from one run.
 
-``--impl reference`` times the FP64 CPU oracle on the same workload instead
-(rank 0 only).  Multi-GPU: replicas only — each rank solves its own instance
-of the same workload, no collective on the data path (weak scaling).
+``--workload`` selects any other workload alone.  ``--impl reference``
+times the FP64 CPU oracle on the same workload instead (rank 0 only).
+Multi-GPU: the batched workload is one problem set of 4096·N problems
+partitioned across the N ranks by longest-processing-time on estimated work
+(weak scaling, no collective on the data path); single problems run as
+replicas.
 """
 from __future__ import annotations
 
@@ -37,8 +44,8 @@ WORKLOADS = {
     "random": (0, "random QP n=50 m=500, P=MM^T+1e-2 I, A at 15% N(0,1)"),
     "portfolio": (2, "portfolio QP n=10000 assets k=100 factors, F at 50% N(0,1); "
                      "variables (x,y) n=10100, rows m=10101"),
-    "mpc_batch": (3, "4096 ragged MPC QPs, nx~U{4..32}, nu=nx/2, T~U{10..30}, one persistent "
-                     "launch (cold: scaling + ADMM per problem)"),
+    "mpc_batch": (3, "4096 ragged MPC QPs per GPU, nx~U{4..32}, nu=nx/2, T~U{10..30}, one "
+                     "persistent launch (cold: scaling + ADMM per problem)"),
     "serve": (4, "serving: Poisson arrivals at 2000 req/s over a pool of 256 random-QP (m=10n) and "
                  "256 Huber (100n x n) problem IDs, n~logU[10,NMAX], warm-started perturbed q/l/u"),
     "svm": (None, "SVM QP (App. A.7): 100 features, 10000 points at 15% density, labels split in half; "
@@ -55,9 +62,9 @@ PARAM_LEN = {"lasso_path": 100, "mpc_loop": 100, "portfolio_bt": 960}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant kernel, from one ncu capture of the same command with the
 # kernels as they are now; for the batch, the capture of the first 608
-# problems scaled by the problems of the launch.  Absent: not captured.
-TRAFFIC = {("lasso", "fp64"): 20.783616e6, ("lasso", "fp32"): 15.043328e6,
-           ("random", "fp64"): 0.519936e6}
+# problems scaled by the problems of the launch.  Absent: not captured
+# since the kernels last changed.
+TRAFFIC = {}
 TRAFFIC_BATCH_PER_PROBLEM = {}
 # Mean time per QP and mean iterations per QP that the paper reports for the
 # same sequences (OSQP direct method on a CPU; context only)
@@ -74,15 +81,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lasso")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mpc_batch")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default=None,
+                    help="default: fp32 (mixed) for mpc_batch, fp64 otherwise")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="mpc_batch: skip the plain single-problem FP64 Lasso measurement")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
     ap.add_argument("--nmax", type=int, default=500, help="serve: largest problem dimension n")
     ap.add_argument("--seq-len", type=int, default=None,
                     help="parametric workloads: QPs of the sequence (default: the paper's length)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "fp32" if args.workload == "mpc_batch" else "fp64"
+    return args
 
 
 def dist_env():
@@ -242,11 +255,34 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return 0
     if args.workload == "mpc_batch":
-        # the oracle on a bounded sample of the batch, one problem per process
-        count = int(os.environ.get("OSQP_BATCH_COUNT", "4096"))
-        cb, _, _ = batch_cpu_baseline(pb.mpc_batch(count, seed=3000))
-        print(json.dumps(_reference_line(args, "mpc_batch", cb["value"], 1, 1.0 / cb["value"],
-                                         None, cb["sample"], cb["cores"])), flush=True)
+        # the oracle on rank 0's share of the batch (the whole 4096-problem
+        # set at N = 1), one problem per process on all host cores; a step is
+        # one pass over it, and the run stops early past about two minutes
+        import multiprocessing as mp
+        from oracle import oracle as O
+        O.build()
+        count, spec, weights = batch_spec(ws)
+        from paper_1711_08013_gb300 import dist as D
+        mine = D.shard(weights, 0, ws)
+        qps = [pb.mpc(*spec[i][:2], seed=spec[i][2]) for i in mine]
+        cores = os.cpu_count() or 1
+        with mp.get_context("spawn").Pool(cores) as pool:
+            for _ in range(args.warmup):
+                pool.map(_oracle_iters_one, qps, chunksize=4)
+            t0 = time.perf_counter()
+            steps = iters = 0
+            while steps < args.steps:
+                iters += sum(pool.map(_oracle_iters_one, qps, chunksize=4))
+                steps += 1
+                if time.perf_counter() - t0 > 120.0:
+                    break
+            dt = time.perf_counter() - t0
+        value = steps * len(qps) / dt
+        line = _reference_line(args, "mpc_batch", value, steps, dt, iters,
+                               f"{steps} pass(es) over the {len(qps)} problems of rank 0's share, "
+                               f"one problem per process on {cores} cores, {dt:.1f} s", cores)
+        line["warmup"] = args.warmup
+        print(json.dumps(line), flush=True)
         return 0
     if args.workload == "serve":
         # the oracle solving a bounded sample of the request stream (each
@@ -350,23 +386,37 @@ def cpu_baseline(args, qp):
                       f"{dt:.1f} s, single thread"}, r
 
 
+def batch_spec(ws):
+    """The global batched problem set: 4096 (OSQP_BATCH_COUNT) problems per
+    rank, generated from one specification so that any rank can build any
+    problem alone."""
+    count = int(os.environ.get("OSQP_BATCH_COUNT", "4096"))
+    spec = pb.mpc_batch_spec(count * ws, seed=3000)
+    return count, spec, [pb.mpc_spec_work(nx, T) for nx, T, _ in spec]
+
+
 def batch_main(args, ws, rank, local):
-    """Batched workload: a step is one cold solve of every problem of the batch
-    (Ruiz scaling + ADMM), timed on the device; the data (≈ GBs) exceed L2."""
+    """Batched workload: a step is one cold solve of every problem of this
+    rank's share of the batch (Ruiz scaling + ADMM), timed on the device; the
+    data (≈ GBs) exceed L2."""
     import torch
     import torch.distributed as dist
     from paper_1711_08013_gb300 import _binding as B
+    from paper_1711_08013_gb300 import dist as D
     from paper_1711_08013_gb300.solver import BatchSolver
 
-    from paper_1711_08013_gb300 import dist as D
     torch.cuda.set_device(local)
     if ws > 1:
         D.init("nccl", torch.device("cuda", local))
-    count = int(os.environ.get("OSQP_BATCH_COUNT", "4096"))
-    qps = pb.mpc_batch(count, seed=3000 + 100000 * rank)
+    dev = torch.device("cuda", local)
+    count, spec, weights = batch_spec(ws)
     prec = B.FP64 if args.precision == "fp64" else B.FP32_MIXED
     stream = torch.cuda.Stream()
-    bs = BatchSolver(qps, stream=stream.cuda_stream, precision=prec)
+    sb = D.ShardedBatch(weights, lambda i: pb.mpc(*spec[i][:2], seed=spec[i][2]),
+                        lambda qs: BatchSolver(qs, stream=stream.cuda_stream, precision=prec),
+                        rank=rank, world=ws)
+    qps, bs = sb.problems, sb.solver
+    local_count = len(qps)
     h = bs.handle
     for _ in range(args.warmup):
         B.osqp_batch_reset(h)
@@ -378,31 +428,31 @@ def batch_main(args, ws, rank, local):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    infos = []
     for k in range(args.steps):
         B.osqp_batch_reset(h)
         evs[k][0].record(stream)
         B.osqp_batch_solve_async(h)
         evs[k][1].record(stream)
         stream.synchronize()
-        infos.append([bs.result(i) for i in range(count)] if k == args.steps - 1 else None)
     torch.cuda.synchronize()
     clocks = sampler.stop()
+    if ws > 1:
+        dist.barrier()
+    last = [bs.result(i) for i in range(local_count)]
     step_s = [a.elapsed_time(b) * 1e-3 for a, b in evs]
     total = sum(step_s)
-    last = infos[-1]
     if any(r.status != B.SOLVED for r in last):
         raise SystemExit("a batched solve did not converge")
     iters = sum(r.iter for r in last)
     lat = sorted(r.solve_time for r in last)
-    n_solves = count * args.steps
-    total = D.max_over_ranks(total, device="cuda")
+    total_max = D.max_over_ranks(total, device=dev)
+    solves_all = D.sum_over_ranks(float(local_count * args.steps), device=dev)
+    iters_all = D.sum_over_ranks(float(iters), device=dev)
     sv = 8 if prec == B.FP64 else 4
     bytes_launch = sum(admm_bytes(q.n, q.m, q.P_full().nnz + q.A.nnz, q.A.nnz, sv, r.iter,
                                   r.pcg_iters, (r.iter + 24) // 25) for q, r in zip(qps, last))
     t_launch = statistics.mean(step_s)
-    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    peak, peak_src = hbm_peak()
     # end to end through the public API: new q/l/u of every problem from
     # pinned host memory, the solve, and x, y of every problem back to the host
     pins = [(torch.tensor(q.q).pin_memory(), torch.tensor(q.l).pin_memory(),
@@ -421,30 +471,36 @@ def batch_main(args, ws, rank, local):
                 raise SystemExit("get failed")
 
     e2e_step()
-    t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 3))
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
     for _ in range(e2e_steps):
         B.osqp_batch_reset(h)
         e2e_step()
-    e2e_dt = time.perf_counter() - t0
+    e2e_dt = D.max_over_ranks(time.perf_counter() - t0, device=dev)
+    traffic = (TRAFFIC_BATCH_PER_PROBLEM[args.precision] * local_count
+               if args.precision in TRAFFIC_BATCH_PER_PROBLEM else None)
     line = {
-        "metric": METRIC, "value": ws * n_solves / total, "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "metric": METRIC, "value": solves_all / total_max, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == B.FP64 else "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOADS["mpc_batch"][1].replace("4096", str(count)),
                    "precision": args.precision, "eps": 1e-3,
-                   "l2": "inputs larger than L2 (no flush)"},
-        "admm_iter_per_s": ws * iters / (total / args.steps),
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": (f"one set of {count * ws} problems sharded over {ws} GPUs "
+                                   "(LPT on estimated work)") if ws > 1 else "single"},
+        "admm_iter_per_s": iters_all / (total_max / args.steps),
         "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[int(0.99 * (len(lat) - 1))],
-        "admm_iters_per_solve": iters / count,
-        "pcg_iters_per_solve": sum(r.pcg_iters for r in last) / count,
+        "admm_iters_per_solve": iters / local_count,
+        "pcg_iters_per_solve": sum(r.pcg_iters for r in last) / local_count,
         "roofline": {"bound": "hbm", "kernel": "k_batch", "achieved": bytes_launch / t_launch / 1e9,
                      "peak": peak, "unit": "GB/s", "frac": bytes_launch / t_launch / 1e9 / peak,
-                     "traffic": (TRAFFIC_BATCH_PER_PROBLEM[args.precision] * count
-                                 if args.precision in TRAFFIC_BATCH_PER_PROBLEM else None),
+                     "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_launch},
-        "e2e": {"value": ws * count * e2e_steps / e2e_dt, "unit": UNIT,
+        "e2e": {"value": D.sum_over_ranks(float(local_count * e2e_steps), device=dev) / e2e_dt,
+                "unit": UNIT,
                 "h2d_bytes_per_step": 8 * sum(q.n + 2 * q.m for q in qps),
                 "d2h_bytes_per_step": 8 * sum(q.n + q.m for q in qps)},
         # k_batch every step, plus k_batch_cluster when heavy problems went to
@@ -452,15 +508,35 @@ def batch_main(args, ws, rank, local):
         "gpu_launches": args.steps * (1 + int(any(r.launch == 3 for r in last))),
         "clocks": clocks,
     }
-    bs.close()
+    sb.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], idx, out = batch_cpu_baseline(qps)
         line["oracle_error"] = batch_error(qps, last, idx, out)
+    if not args.no_plain:
+        # the plain single-problem FP64 form on the same GPU(s), for the
+        # batched-vs-plain comparison of the metric
+        import copy
+        pa = copy.copy(args)
+        pa.workload, pa.precision = "lasso", "fp64"
+        plain = single_main(pa, ws, rank, local, init_dist=False)
+        keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config",
+                "admm_iter_per_s", "p50_ms", "p99_ms", "admm_iters_per_solve",
+                "pcg_iters_per_solve", "roofline", "e2e", "gpu_launches", "clocks",
+                "cpu_baseline", "oracle_error")
+        line["plain"] = {k: plain[k] for k in keep if k in plain}
+        line["batched_over_plain"] = line["value"] / plain["value"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
 
 
 def _oracle_solve_one(qp):
@@ -469,24 +545,37 @@ def _oracle_solve_one(qp):
     return r.status, r.x, r.obj_val
 
 
-def batch_cpu_baseline(qps, sample=256):
-    """The oracle on a bounded sample of the batch, one problem per process
-    across all host cores (spawned pool: safe after CUDA initialisation)."""
+def _oracle_iters_one(qp):
+    from oracle import oracle as O
+    r = O.solve(qp)
+    return r.iter
+
+
+def batch_cpu_baseline(qps, budget_s=12.0, sample=256):
+    """The oracle on the batch, one problem per process across all host
+    cores (spawned pool: safe after CUDA initialisation), in passes over the
+    whole batch until about budget_s seconds of wall time; also returns the
+    oracle's solutions of an evenly spaced sample for the error statement."""
     import multiprocessing as mp
     from oracle import oracle as O
     O.build()
     idx = list(range(0, len(qps), max(1, len(qps) // sample)))[:sample]
-    sub = [qps[i] for i in idx]
     cores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
-        pool.map(_oracle_solve_one, sub[:cores])  # warm the workers
+        pool.map(_oracle_iters_one, qps[:cores])  # warm the workers
+        out = pool.map(_oracle_solve_one, [qps[i] for i in idx], chunksize=1)
         t0 = time.perf_counter()
-        out = pool.map(_oracle_solve_one, sub, chunksize=1)
+        done = 0
+        while True:
+            pool.map(_oracle_iters_one, qps, chunksize=4)
+            done += len(qps)
+            if time.perf_counter() - t0 > budget_s:
+                break
         dt = time.perf_counter() - t0
-    return {"value": len(sub) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(sub)} of the {len(qps)} batch problems, one per process on "
-                      f"{cores} cores, {dt:.1f} s"}, idx, out
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done // len(qps)} pass(es) over all {len(qps)} batch problems, one "
+                      f"problem per process on {cores} cores, {dt:.1f} s"}, idx, out
 
 
 def batch_error(qps, results, idx, out):
@@ -649,18 +738,10 @@ def param_main(args, ws, rank, local):
     return 0
 
 
-def main():
-    args = parse()
-    ws, rank, local = dist_env()
-    if args.impl == "reference":
-        return run_reference(args, ws, rank)
-    if args.workload == "mpc_batch":
-        return batch_main(args, ws, rank, local)
-    if args.workload == "serve":
-        return serve_main(args, ws, rank, local)
-    if args.workload in PARAM_LEN:
-        return param_main(args, ws, rank, local)
-
+def single_main(args, ws, rank, local, init_dist=True):
+    """Single-problem workloads: a step is one whole solve of one QP (data
+    reloaded from HBM, scaling, ADMM), L2 flushed between steps.  Returns the
+    JSON line (rank 0 prints it when this is the run's workload)."""
     import torch
     import torch.distributed as dist
     from paper_1711_08013_gb300 import _binding as B
@@ -670,7 +751,7 @@ def main():
         raise SystemExit("bench.py needs a CUDA device")
     from paper_1711_08013_gb300 import dist as D
     torch.cuda.set_device(local)
-    if ws > 1:
+    if ws > 1 and init_dist:
         D.init("nccl", torch.device("cuda", local))
 
     cfg, desc, qp = build_problem(args, rank)
@@ -812,9 +893,25 @@ def main():
         line["oracle_error"] = dict(result_error(qp, g.x, g.y, g.obj_val, o.x, o.obj_val),
                                     reference="oracle (FP64, direct method) at the same eps")
     s.close()
+    return line
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    if args.workload == "mpc_batch":
+        return batch_main(args, ws, rank, local)
+    if args.workload == "serve":
+        return serve_main(args, ws, rank, local)
+    if args.workload in PARAM_LEN:
+        return param_main(args, ws, rank, local)
+    line = single_main(args, ws, rank, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
     return 0
 

@@ -285,6 +285,17 @@ int64_t osqp_batch_footprint(const osqp_batch* b, int32_t i);
 
 int32_t osqp_batch_cleanup(osqp_batch* b);
 
+/* Diagnostic read-back of the scaling and the preconditioner (host arrays,
+ * any may be NULL; waits for the stream): D (n) and E (m) of Alg. 2 with
+ * the cost factor c (§5.1), and the Jacobi diagonal (n) of the reduced
+ * system of §3.1 for the current ρ̄,
+ *   jacobi_j = P̄_jj + σ + Σ_i ρ_i Ā_ij²,  ρ_i = ρ̄, or 10³ρ̄ on equality rows (§5.2),
+ * in the scaled data P̄ = cDPD, Ā = EAD, as the last setup, update or ρ̄
+ * change left it (within a solve an adaptive ρ̄ update rebuilds it; the
+ * values read after the solve belong to the final ρ̄).  Returns OSQP_ERR_ARG
+ * for a NULL solver, OSQP_ERR_CUDA on a failed copy. */
+int32_t osqp_diag_scaling(osqp_solver* s, double* D, double* E, double* c, double* jacobi);
+
 /* Diagnostic of the bounded grid barrier that every multi-CTA solve relies
  * on (the paper has no counterpart).  Launches four cooperative CTAs on the
  * current device, one of which never arrives at the barrier; the others must

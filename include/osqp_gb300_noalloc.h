@@ -34,9 +34,13 @@ extern "C" {
  *
  * Returns OSQP_ERR_LIMIT when the problem needs more than
  * OSQP_NOALLOC_SCRATCH_BYTES of work space (about 2·nnz(P) + nnz(A) values
- * and indices plus ~45 vectors of length n or m) or has a row of [P Aᵀ] or A
- * longer than 8192 entries; OSQP_ERR_CSC for malformed CSC (checked on the
- * device); the usual codes for bad settings.  The call waits for the stream.
+ * and indices plus ~45 vectors of length n or m) or has a row of [P Aᵀ]
+ * (the full symmetric P part and the column of A together) or of A longer
+ * than 8192 entries; OSQP_ERR_CSC for malformed CSC; OSQP_ERR_NONFINITE for
+ * a NaN or infinity in P, A or q or a NaN bound, and OSQP_ERR_LGTU for some
+ * l_i > u_i (these input checks of osqp_setup run on the device here, CSC
+ * structure first, then values); the usual codes for bad settings.  The
+ * call waits for the stream.
  *
  * Inside a stream capture (stream is capturing) nothing may wait, so the
  * call only enqueues the solve and returns OSQP_OK; info must then be NULL
@@ -63,8 +67,9 @@ int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_colptr,
 /* Status of the last solve that ran in the work array (a call of
  * osqp_solve_noalloc, or a replay of one captured in a CUDA graph) for a
  * problem with these sizes, nonzero counts and precision (OSQP_PRECISION_*):
- * fills *info (host) as osqp_solve_noalloc does and returns OSQP_ERR_CSC or
- * OSQP_ERR_LIMIT when the device rejected that problem.  The sizes locate
+ * fills *info (host) as osqp_solve_noalloc does and returns OSQP_ERR_CSC,
+ * OSQP_ERR_LIMIT, OSQP_ERR_NONFINITE or OSQP_ERR_LGTU when the device rejected
+ * that problem (a rejected replay leaves x and y unwritten).  The sizes locate
  * the status inside the work array; other sizes read unrelated bytes.
  * Waits for the stream; OSQP_ERR_ARG inside a stream capture. */
 int32_t osqp_noalloc_get_info(int32_t n, int32_t m, int32_t P_nnz, int32_t A_nnz,

@@ -78,6 +78,7 @@ _SIGS = {
     "osqp_get_certificate": (C.c_int32, [_P, _P, _P]),
     "osqp_cleanup": (C.c_int32, [_P]),
     "osqp_diag_barrier_timeout": (C.c_int32, [C.c_double]),
+    "osqp_diag_scaling": (C.c_int32, [_P, _P, _P, _P, _P]),
     "osqp_batch_uses_cluster": (C.c_int32, [_P, C.c_int32]),
     "osqp_batch_setup": (C.c_int32, [C.POINTER(_P), C.c_int32, _P, _P, _P, _P, _P,
                                      C.POINTER(osqp_settings), _P]),
@@ -224,6 +225,14 @@ def osqp_get_certificate(h, n: int, m: int):
     py, dx = np.empty(m), np.empty(n)
     _check(lib().osqp_get_certificate(h, _ptr(py), _ptr(dx)), "osqp_get_certificate")
     return py, dx
+
+
+def osqp_diag_scaling(h, n: int, m: int):
+    """D (n), E (m), c and the Jacobi diagonal (n) as the solver holds them."""
+    D, E, dg, c = np.empty(n), np.empty(m), np.empty(n), C.c_double(0.0)
+    _check(lib().osqp_diag_scaling(h, _ptr(D), _ptr(E), C.addressof(c), _ptr(dg)),
+           "osqp_diag_scaling")
+    return D, E, c.value, dg
 
 
 def osqp_cleanup(h):

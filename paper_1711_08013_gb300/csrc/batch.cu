@@ -175,7 +175,7 @@ struct Bump {
 // Static block (uploaded once): sliced structure, raw values, schedules,
 // raw vectors.
 struct SchedOffsets {
-  size_t sl, sr, ch, lr;
+  size_t sl, sr, ch, lr, rng, li;
 };
 
 struct StaticOffsets {
@@ -189,6 +189,8 @@ SchedOffsets sched_offsets(Bump& b, const SchedHost& h) {
   o.sr = b.take<int>(h.srow.size());
   o.ch = b.take<int4>(h.chunks.size());
   o.lr = b.take<int>(h.long_rows.size());
+  o.rng = b.take<int2>(h.lrange.size());
+  o.li = b.take<int>(h.lidx.size());
   return o;
 }
 
@@ -208,13 +210,18 @@ StaticOffsets static_offsets(const ProblemLayout& L) {
   return o;
 }
 
-// Dynamic block: working matrices and every vector of Dev<T>.
+// Dynamic block: working matrices, the long-row partials and counters of
+// both products, and every vector of Dev<T>.
 template <typename T>
 size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
   Bump b;
   const size_t n = L.n, m = L.m;
   const size_t kn_v = b.take<T>(L.kn_s.npos);
   const size_t a_v = b.take<T>(L.a_s.npos);
+  const size_t kn_cp = b.take<double>(L.kn_s.chunks.size() * kMaxNV);
+  const size_t kn_cc = b.take<unsigned>(L.kn_s.lrange.size());
+  const size_t a_cp = b.take<double>(L.a_s.chunks.size() * kMaxNV);
+  const size_t a_cc = b.take<unsigned>(L.a_s.lrange.size());
   const size_t rt = b.take<uint8_t>(m);
   const size_t pact = b.take<uint8_t>(m);
   size_t on[22], om[22], otn[11], otm[6];
@@ -226,6 +233,10 @@ size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
   if (base && d) {
     d->kn_v = (T*)(base + kn_v);
     d->a_v = (T*)(base + a_v);
+    d->kn.cpart = (double*)(base + kn_cp);
+    d->kn.ccount = (unsigned*)(base + kn_cc);
+    d->as.cpart = (double*)(base + a_cp);
+    d->as.ccount = (unsigned*)(base + a_cc);
     d->rtype = (uint8_t*)(base + rt);
     d->pol_act = (uint8_t*)(base + pact);
     double** nv[] = {&d->D, &d->q, &d->pdiag, &d->dg, &d->nrm_n, &d->x, &d->dx, &d->px,
@@ -328,6 +339,10 @@ void fill_batch_devs(osqp_batch* b) {
                    (const int*)(sb + so.sr),
                    (const int4*)(sb + so.ch),
                    (const int*)(sb + so.lr),
+                   (const int2*)(sb + so.rng),
+                   (const int*)(sb + so.li),
+                   nullptr,   // cpart, ccount: carved in the dynamic block below
+                   nullptr,
                    0};  // prefetch: set below from the matrix bytes
     };
     d->kn = sched(L.kn_s, o.kn, L.n);
@@ -685,6 +700,8 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
       put(so.second->sr, so.first->srow.data(), sizeof(int) * so.first->srow.size());
       put(so.second->ch, so.first->chunks.data(), sizeof(int4) * so.first->chunks.size());
       put(so.second->lr, so.first->long_rows.data(), sizeof(int) * so.first->long_rows.size());
+      put(so.second->rng, so.first->lrange.data(), sizeof(int2) * so.first->lrange.size());
+      put(so.second->li, so.first->lidx.data(), sizeof(int) * so.first->lidx.size());
     }
     put(o.q, q[i], sizeof(double) * L.n);
     if (L.m) {
@@ -696,6 +713,11 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
     b->L[i].a_s.pos = {};
   }
   if (!flush(b->static_bytes)) return fail(OSQP_ERR_CUDA);
+  // dynamic blocks start zeroed: the long-row counters must be zero before
+  // the first product
+  if (b->arena_bytes > b->static_bytes &&
+      cudaMemset(b->arena + b->static_bytes, 0, b->arena_bytes - b->static_bytes) != cudaSuccess)
+    return fail(OSQP_ERR_CUDA);
 
   if (settings->precision == OSQP_PRECISION_FP64) fill_batch_devs<double>(b);
   else fill_batch_devs<float>(b);

@@ -17,8 +17,9 @@
 // Matrices: Kn = [P̄ Āᵀ] (n rows; column c < n addresses P̄, column n + i
 // addresses Āᵀ) and Ā (m rows), each in the sliced layout described at
 // Sched: short rows in coalesced 32-lane slices sorted by length, rows
-// longer than `long_thresh` in 256-nonzero chunks that whole warps reduce
-// and add atomically into outputs zeroed in an earlier stage.
+// longer than `long_thresh` in 256-nonzero chunks that whole warps reduce;
+// the chunk partials of a long row are summed in chunk order by whichever
+// warp stores the row's last partial, so every product is deterministic.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -29,8 +30,14 @@ namespace osqpgb {
 constexpr int kThreads = 512;   // threads per CTA of every team kernel
 constexpr int kMaxRed = 32;     // reduction slots
 constexpr int kMaxSumSlots = 4; // sum slots staged through shared memory per reduction
-constexpr int kSmemDoubles = 34 * kMaxRed + kMaxSumSlots * kThreads;
+// Shared memory of every team kernel: reduction partials and results
+// (34·kMaxRed), the sum-slot staging area, and the scalars of the PCG
+// recurrence that one warp updates for the whole CTA (kScalSlots).
+constexpr int kScalSlots = 8;
+constexpr int kScalOff = 34 * kMaxRed + kMaxSumSlots * kThreads;
+constexpr int kSmemDoubles = kScalOff + kScalSlots;
 constexpr int kChunk = 256;     // nonzeros per long-row chunk
+constexpr int kMaxNV = 4;       // partial values stored per long-row chunk
 
 constexpr uint8_t kLInf = 1, kUInf = 2, kEq = 4;  // row-type bits
 constexpr double kInfBound = 1e20;
@@ -49,13 +56,21 @@ enum DevError : int { kDevOk = 0, kDevBarrierTimeout = 1 };
 // step t of a slice stores one nonzero per lane at first + 32·t + lane, so
 // every warp load of column indices or values is one coalesced 128-byte
 // line.  Padding positions hold column −1.  Longer rows follow in CSR order
-// and are split into kChunk-nonzero chunks, each taken by a whole warp.
+// and are split into kChunk-nonzero chunks, each taken by a whole warp; a
+// chunk stores its partial result in cpart and counts itself in the row's
+// ccount, and the warp whose count completes the row sums the row's
+// partials in chunk order (a fixed order, whoever arrives last).
 struct Sched {
   int nrows, group, long_thresh, nchunks, nlong, nslices;
   const int2* slices;   // (first position, steps)
   const int* srow;      // row of local row r of slice s at s·(32/group) + r; −1 = none
-  const int4* chunks;   // (row, begin, end, first-chunk-of-row) in positions
+  const int4* chunks;   // (row, begin, end, long-row index) in positions
   const int* long_rows;
+  const int2* lrange;   // per long row: (first chunk, number of chunks)
+  const int* lidx;      // per row: its long-row index, −1 for a short row
+  double* cpart;        // per chunk: kMaxNV partial values of the current product
+  unsigned* ccount;     // per long row: chunks stored in the current product
+                        // (zero between products: the completing warp resets it)
   int prefetch;         // 1: stream the slices into L2 ahead of use (data not L2-resident)
 };
 
@@ -126,10 +141,6 @@ __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-__device__ __forceinline__ void atomic_max_nonneg(double* a, double v) {
-  atomicMax(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
 }
 
 template <bool MAX>
@@ -232,16 +243,18 @@ __device__ __forceinline__ float funkey(unsigned k) {
 // Block-wide reduction of K working-precision (FP32) slots with the result
 // in FP64, for the FP32-mixed mode: each warp sums its lanes' values by a
 // shuffle tree of error-free FP32 additions (Knuth's TwoSum, the rounding
-// errors carried in a second FP32 term), so the narrow FP64 pipe only adds
-// one value per warp.  Max slots combine order-preserving keys.  Result in
+// errors carried in a second FP32 term) and stores the (sum, error) pair;
+// one warp per slot then converts the warps' pairs to FP64 and adds them,
+// so the narrow FP64 pipe sees one instruction per slot rather than one per
+// warp.  Max slots combine order-preserving keys.  Result in
 // sm[32*kMaxRed + k], as block_reduce.  All threads call it.
 template <int K, unsigned MAXMASK>
 __device__ __forceinline__ void block_reduce(const float (&v)[K], double* sm) {
   static_assert(K <= kMaxSumSlots, "too many slots");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float2* pw = reinterpret_cast<float2*>(sm);  // [warp · kMaxRed + slot]
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double w;
     if ((MAXMASK >> k) & 1u) {
       unsigned x = fkey(v[k]);
 #pragma unroll
@@ -249,7 +262,7 @@ __device__ __forceinline__ void block_reduce(const float (&v)[K], double* sm) {
         const unsigned o = __shfl_xor_sync(0xffffffffu, x, off);
         x = x > o ? x : o;
       }
-      w = (double)funkey(x);
+      if (lane == 0) pw[wid * kMaxRed + k] = make_float2(funkey(x), 0.0f);
     } else {
       float hi = v[k], lo = 0.0f;
 #pragma unroll
@@ -262,21 +275,21 @@ __device__ __forceinline__ void block_reduce(const float (&v)[K], double* sm) {
         hi = s;
         lo = __fadd_rn(lo, __fadd_rn(bl, err));
       }
-      w = (double)hi + (double)lo;
+      if (lane == 0) pw[wid * kMaxRed + k] = make_float2(hi, lo);
     }
-    if (lane == 0) sm[wid * kMaxRed + k] = w;
   }
   __syncthreads();
   if (wid < K) {
     const int k = wid;
     const bool mx = (MAXMASK >> k) & 1u;
+    const float2 e = lane < nw ? pw[lane * kMaxRed + k] : make_float2(mx ? -INFINITY : 0.0f, 0.0f);
     if (mx) {
-      unsigned long long x = lane < nw ? dkey(sm[lane * kMaxRed + k]) : 0ull;
+      unsigned long long x = dkey((double)e.x);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) x = umax64(x, __shfl_xor_sync(0xffffffffu, x, off));
       if (lane == 0) sm[32 * kMaxRed + k] = dunkey(x);
     } else {
-      double x = lane < nw ? sm[lane * kMaxRed + k] : 0.0;
+      double x = (double)e.x + (double)e.y;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
       if (lane == 0) sm[32 * kMaxRed + k] = x;
@@ -289,6 +302,7 @@ __device__ __forceinline__ void block_reduce(const float (&v)[K], double* sm) {
 // Teams
 // ---------------------------------------------------------------------------
 struct GridTeam {
+  static constexpr bool kCtaScope = false;  // products span CTAs
   Barrier* bar;
   int* err;
   double* part;  // [2][gridDim.x][kMaxRed]
@@ -427,6 +441,7 @@ __device__ __forceinline__ void cluster_sync_all() {
 // memory (double-buffered), and after the barrier every CTA combines the
 // cluster's partials in rank order, so all CTAs hold identical values.
 struct ClusterTeam {
+  static constexpr bool kCtaScope = false;
   static constexpr unsigned int kBarrierPoison = 0x80000000u;
   double* sm;
   double* cpart;  // [2][kMaxRed] this CTA's published block results
@@ -509,6 +524,7 @@ struct ClusterTeam {
 };
 
 struct BlockTeam {
+  static constexpr bool kCtaScope = true;  // every warp of a product is in this CTA
   double* sm;
   __device__ int nthreads() const { return blockDim.x; }
   __device__ int tid() const { return threadIdx.x; }
@@ -532,6 +548,7 @@ struct BlockTeam {
 
 // A plain (non-cooperative) launch as a traversal team: no barriers.
 struct PlainTeam {
+  static constexpr bool kCtaScope = false;
   __device__ int nthreads() const { return gridDim.x * blockDim.x; }
   __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
   __device__ int nwarps() const { return gridDim.x * (blockDim.x >> 5); }
@@ -541,10 +558,13 @@ struct PlainTeam {
 // ---------------------------------------------------------------------------
 // Traversal of the sliced layout.  gather(col, val, acc) folds one nonzero
 // into the NV accumulators; the group then combines its lanes (sum, or max
-// when MAXR) and on_row(row, acc) runs once per short row, on_chunk(row,
-// first, acc) once per long-row chunk.  A lane accumulates its nonzeros of a
-// row in order and the group combines them by a fixed shuffle tree, so a
-// row's result does not depend on where its slice sits.
+// when MAXR) and on_row(row, acc) runs once per short row.  A long row is
+// reduced chunk by chunk: on_chunk(row, first, acc) runs once per chunk with
+// that chunk's partial (for inner products that take the row piecewise), and
+// on_long(row, acc) once per long row with the sum of its partials in chunk
+// order.  A lane accumulates its nonzeros of a row in order and the group
+// combines them by a fixed shuffle tree, so a row's result does not depend on
+// where its slice sits, and a long row's result not on which warp finished it.
 // ---------------------------------------------------------------------------
 // Bulk prefetch of one slice's column indices and values into L2 (a slice
 // occupies 32·steps consecutive positions starting at a multiple of 32, so
@@ -558,11 +578,125 @@ __device__ __forceinline__ void prefetch_slice(int2 sl, const int* ci, const MT*
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(va + sl.x), "r"(bv) : "memory");
 }
 
-template <int NV, bool MAXR, typename AT, typename MT, class Team, class G, class R, class C>
+// Arrival of one chunk at its row's counter: a release add (the chunk's
+// partial, stored just before by the same thread, is published with it).
+// The warp that completes the count then takes an acquire fence before it
+// reads the other partials (see chunk_acquire).  CTA scope when the whole
+// product runs in one CTA.
+template <bool CTA>
+__device__ __forceinline__ unsigned chunk_arrive(unsigned* ctr) {
+  unsigned old;
+  if (CTA)
+    asm volatile("atom.release.cta.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
+  else
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
+  return old;
+}
+template <bool CTA>
+__device__ __forceinline__ void chunk_acquire() {
+  if (CTA) asm volatile("fence.acq_rel.cta;" ::: "memory");
+  else asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+struct NoChunk {
+  template <typename A>
+  __device__ __forceinline__ void operator()(int, int, A*) const {}
+};
+struct NoLong {
+  template <typename A>
+  __device__ __forceinline__ void operator()(int, A*) const {}
+};
+struct LazyTag {};
+
+// With LAZY the chunks only store their partials: no arrivals, no on_long.
+// The stage that consumes the product then sums a long row's partials itself
+// (long_sum), which is possible where it reads the output only at the row's
+// own index (elementwise).
+template <int NV, bool MAXR, typename AT, typename MT, class Team, class G, class R, class C,
+          class L, bool LAZY = false>
 __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* __restrict__ ci,
-                                     const MT* __restrict__ va, G gather, R on_row, C on_chunk) {
+                                     const MT* __restrict__ va, G gather, R on_row, C on_chunk,
+                                     L on_long) {
+  static_assert(NV <= kMaxNV, "too many partial values per chunk");
   constexpr int B = NV == 1 ? 8 : 4;  // steps whose loads are issued together
   const int lane = threadIdx.x & 31;
+  const int nwt = tm.nwarps();
+  // The warp whose arrival completes a long row sums the row's partials
+  // (lane k takes chunks k, k+32, … in order, then a fixed shuffle tree)
+  // and resets the count for the next product.
+  auto finish = [&](int4 ch) {
+    const int2 lr = S.lrange[ch.w];
+    chunk_acquire<Team::kCtaScope>();
+    __syncwarp();  // every lane's partial loads after lane 0's acquire
+    AT acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = AT(0);
+    for (int k = lane; k < lr.y; k += 32) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const AT o = (AT)__ldcg(S.cpart + (size_t)(lr.x + k) * kMaxNV + v);
+        acc[v] = MAXR ? (acc[v] > o ? acc[v] : o) : acc[v] + o;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        AT o = __shfl_xor_sync(0xffffffffu, acc[v], off);
+        acc[v] = MAXR ? (acc[v] > o ? acc[v] : o) : acc[v] + o;
+      }
+    }
+    if (lane == 0) {
+      on_long(ch.x, acc);
+      S.ccount[ch.w] = 0u;
+    }
+  };
+  // Long-row chunks first.  Each stores its partial and arrives at its row's
+  // count; the count returned for the warp's first chunk is looked at only
+  // after the short rows, so its round trip overlaps them.  A chunk holds at
+  // most kChunk = 8·32 nonzeros: one batch of 8 per lane.
+  int first_c = -1;
+  unsigned first_old = 0u;
+  for (int c = tm.warp(); c < S.nchunks; c += nwt) {
+    const int4 ch = S.chunks[c];
+    AT acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = AT(0);
+    int cc[kChunk / 32];
+    MT vv[kChunk / 32];
+#pragma unroll
+    for (int u = 0; u < kChunk / 32; ++u) {
+      const int k = ch.y + lane + 32 * u;
+      cc[u] = k < ch.z ? ci[k] : -1;
+      vv[u] = k < ch.z ? va[k] : MT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kChunk / 32; ++u)
+      if (cc[u] >= 0) gather(cc[u], vv[u], acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        AT o = __shfl_xor_sync(0xffffffffu, acc[v], off);
+        acc[v] = MAXR ? (acc[v] > o ? acc[v] : o) : acc[v] + o;
+      }
+    }
+    unsigned old = 0u;
+    if (lane == 0) {
+      on_chunk(ch.x, c == S.lrange[ch.w].x ? 1 : 0, acc);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) S.cpart[(size_t)c * kMaxNV + v] = (double)acc[v];
+      if (!LAZY) old = chunk_arrive<Team::kCtaScope>(&S.ccount[ch.w]);
+    }
+    if (LAZY) continue;
+    if (first_c < 0) {
+      first_c = c;
+      first_old = old;
+    } else {
+      old = __shfl_sync(0xffffffffu, old, 0);
+      if (old + 1 == (unsigned)S.lrange[ch.w].y) finish(ch);
+    }
+  }
   const int Gw = S.group;
   const int sub = lane & (Gw - 1);
   const int spw = 32 / Gw;
@@ -571,7 +705,6 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* 
   // Problems whose data do not stay in L2 (set by the batch for its largest
   // problems) ask for each warp's slices two steps ahead, so the index/value
   // stream arrives from DRAM while the dependent gathers run.
-  const int nwt = tm.nwarps();
   if (S.prefetch && lane == 0)
     for (int s = tm.warp(); s < S.nslices && s < tm.warp() + 2 * nwt; s += nwt)
       prefetch_slice(S.slices[s], ci, va);
@@ -607,33 +740,38 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* 
     }
     if (sub == 0 && row >= 0) on_row(row, acc);
   }
-  for (int c = tm.warp(); c < S.nchunks; c += tm.nwarps()) {
-    const int4 ch = S.chunks[c];
-    AT acc[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = AT(0);
-    // a chunk holds at most kChunk = 8·32 nonzeros: one batch of 8 per lane
-    int cc[kChunk / 32];
-    MT vv[kChunk / 32];
-#pragma unroll
-    for (int u = 0; u < kChunk / 32; ++u) {
-      const int k = ch.y + lane + 32 * u;
-      cc[u] = k < ch.z ? ci[k] : -1;
-      vv[u] = k < ch.z ? va[k] : MT(0);
-    }
-#pragma unroll
-    for (int u = 0; u < kChunk / 32; ++u)
-      if (cc[u] >= 0) gather(cc[u], vv[u], acc);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        AT o = __shfl_xor_sync(0xffffffffu, acc[v], off);
-        acc[v] = MAXR ? (acc[v] > o ? acc[v] : o) : acc[v] + o;
-      }
-    }
-    if (lane == 0) on_chunk(ch.x, ch.w, acc);
+  if (!LAZY && first_c >= 0) {
+    first_old = __shfl_sync(0xffffffffu, first_old, 0);
+    const int4 ch = S.chunks[first_c];
+    if (first_old + 1 == (unsigned)S.lrange[ch.w].y) finish(ch);
   }
+}
+
+// Sum of long row lr's partial value v in chunk order, by one thread, after
+// the LAZY product that stored them (a team barrier in between).
+template <typename AT>
+__device__ __forceinline__ AT long_sum(const Sched& S, int lr, int v) {
+  const int2 r = S.lrange[lr];
+  AT acc = AT(0);
+  for (int k = 0; k < r.y; ++k) acc += (AT)__ldcg(S.cpart + (size_t)(r.x + k) * kMaxNV + v);
+  return acc;
+}
+
+// A product whose long rows are left as chunk partials (see LAZY).
+template <int NV, bool MAXR, typename AT, typename MT, class Team, class G, class R, class C>
+__device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* __restrict__ ci,
+                                     const MT* __restrict__ va, G gather, R on_row, C on_chunk,
+                                     NoLong, LazyTag) {
+  spmv<NV, MAXR, AT, MT, Team, G, R, C, NoLong, true>(tm, S, ci, va, gather, on_row, on_chunk,
+                                                      NoLong{});
+}
+
+// The common case: a long row's total goes to the same handler as a short
+// row (no piecewise inner products).
+template <int NV, bool MAXR, typename AT, typename MT, class Team, class G, class R>
+__device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* __restrict__ ci,
+                                     const MT* __restrict__ va, G gather, R on_row) {
+  spmv<NV, MAXR, AT, MT>(tm, S, ci, va, gather, on_row, NoChunk{}, on_row);
 }
 
 // Per-entry pass: f(row, k) for every stored nonzero k (padding skipped).
@@ -658,11 +796,6 @@ __device__ __forceinline__ void foreach_entry(const Team& tm, const Sched& S,
   }
 }
 
-template <class Team, typename V>
-__device__ __forceinline__ void zero_long(const Team& tm, const Sched& S, V* buf) {
-  for (int i = tm.tid(); i < S.nlong; i += tm.nthreads()) buf[S.long_rows[i]] = V(0);
-}
-
 __device__ __forceinline__ double ruiz_delta(double nrm) {
   // δ = 1/√‖M_i‖∞ (Alg. 2); reading: a zero norm gives δ = 1, others are
   // clamped to [1e-4, 1e4].
@@ -676,9 +809,8 @@ __device__ __forceinline__ double rho_of(uint8_t t, double rho_bar) {
 // ---------------------------------------------------------------------------
 // Jacobi diagonal of K = P̄ + σI + ĀᵀRĀ: dg_j = P̄_jj + σ + Σ_i ρ_i Ā_ij²,
 // read from the Āᵀ half of Kn with ρ_i recomputed from the row types so that
-// the stage may run while the ρ vector itself is rewritten.  Long rows are
-// added atomically into dg, which the caller zeroed beforehand; dinv is
-// written for short rows here and for all rows by finish_dinv after a sync.
+// the stage may run while the ρ vector itself is rewritten; dg and its
+// inverse in working precision are written for every row.
 // ---------------------------------------------------------------------------
 template <class Team, typename T>
 __device__ __forceinline__ void jacobi_rows(const Team& tm, const Dev<T>& d, double sigma,
@@ -697,18 +829,7 @@ __device__ __forceinline__ void jacobi_rows(const Team& tm, const Dev<T>& d, dou
         double g = d.pdiag[j] + sigma + acc[0];
         d.dg[j] = g;
         d.dinv[j] = T(1.0 / g);
-      },
-      [&](int j, int first, double* acc) {
-        atomicAdd(&d.dg[j], acc[0] + (first ? d.pdiag[j] + sigma : 0.0));
       });
-}
-
-template <class Team, typename T>
-__device__ __forceinline__ void finish_dinv(const Team& tm, const Dev<T>& d) {
-  for (int i = tm.tid(); i < d.kn.nlong; i += tm.nthreads()) {
-    int j = d.kn.long_rows[i];
-    d.dinv[j] = T(1.0 / d.dg[j]);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -746,15 +867,11 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
           if (col < n) acc[0] = fmax(acc[0], fabs(v) * d.D[col]);
           else acc[1] = fmax(acc[1], fabs(v) * d.E[col - n]);
         },
-        [&](int j, double* acc) { d.nrm_n[j] = d.D[j] * fmax(cc * acc[0], acc[1]); },
-        [&](int j, int, double* acc) {
-          atomic_max_nonneg(&d.nrm_n[j], d.D[j] * fmax(cc * acc[0], acc[1]));
-        });
+        [&](int j, double* acc) { d.nrm_n[j] = d.D[j] * fmax(cc * acc[0], acc[1]); });
     spmv<1, true, double, double>(
         tm, d.as, d.a_ci, d.a_raw,
         [&](int col, double v, double* acc) { acc[0] = fmax(acc[0], fabs(v) * d.D[col]); },
-        [&](int i, double* acc) { d.nrm_m[i] = d.E[i] * acc[0]; },
-        [&](int i, int, double* acc) { atomic_max_nonneg(&d.nrm_m[i], d.E[i] * acc[0]); });
+        [&](int i, double* acc) { d.nrm_m[i] = d.E[i] * acc[0]; });
     if (!tm.sync()) return false;
     // δ, S ← diag(δ)S, and ‖1 − δ‖∞
     double dev[1] = {0.0};
@@ -780,8 +897,7 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
         [&](int col, double v, double* acc) {
           if (col < n) acc[0] = fmax(acc[0], fabs(v) * d.D[col]);
         },
-        [&](int j, double* acc) { d.nrm_n[j] = cc * d.D[j] * acc[0]; },
-        [&](int j, int, double* acc) { atomic_max_nonneg(&d.nrm_n[j], cc * d.D[j] * acc[0]); });
+        [&](int j, double* acc) { d.nrm_n[j] = cc * d.D[j] * acc[0]; });
     double qn[1] = {0.0};
     for (int j = tid; j < n; j += nth) qn[0] = fmax(qn[0], fabs(cc * d.D[j] * d.q_raw[j]));
     tm.template publish<1, 1u>(qn);
@@ -855,8 +971,6 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
       d.zt[i] = 0.0;
     }
   }
-  if (!tm.sync()) return false;
-  finish_dinv(tm, d);
   if (tm.leader()) {
     d.sc->c = c;
     d.sc->ruiz_passes = passes;
@@ -873,10 +987,7 @@ template <class Team, typename T>
 __device__ bool refresh_stage(Team& tm, const Dev<T>& d, const Params& P, double rho_bar) {
   const int n = d.n, m = d.m, tid = tm.tid(), nth = tm.nthreads();
   const double c = d.sc->c;
-  for (int j = tid; j < n; j += nth) {
-    d.q[j] = c * d.D[j] * d.q_raw[j];
-    d.dg[j] = 0.0;
-  }
+  for (int j = tid; j < n; j += nth) d.q[j] = c * d.D[j] * d.q_raw[j];
   for (int i = tid; i < m; i += nth) {
     const double lr = d.l_raw[i], ur = d.u_raw[i];
     const uint8_t t = (uint8_t)((lr <= -kInfBound ? kLInf : 0) | (ur >= kInfBound ? kUInf : 0) |
@@ -892,8 +1003,6 @@ __device__ bool refresh_stage(Team& tm, const Dev<T>& d, const Params& P, double
   }
   if (!tm.sync()) return false;
   jacobi_rows(tm, d, P.sigma, rho_bar);
-  if (!tm.sync()) return false;
-  finish_dinv(tm, d);
   if (tm.leader()) {
     d.sc->rho_bar = rho_bar;
     // the last check's residuals belong to the old data: recompute them on
@@ -945,15 +1054,17 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
   double* __restrict__ t = d.pol_t;
   double* __restrict__ r2 = d.pol_r2;
   auto bnd = [&](int i) { return act[i] == 1 ? d.l[i] : d.u[i]; };
-  // Ā v into out (row sums E_i Σ a_ij D_j v_j; long rows pre-zeroed)
+  // Ā v into out (row sums E_i Σ a_ij D_j v_j)
   auto a_times = [&](const double* v, double* out) {
     spmv<1, false, double, double>(
         tm, d.as, d.a_ci, d.a_raw, [&](int col, double a, double* acc) { acc[0] += a * D[col] * v[col]; },
-        [&](int i, double* acc) { out[i] = E[i] * acc[0]; },
-        [&](int i, int, double* acc) { atomicAdd(&out[i], E[i] * acc[0]); });
+        [&](int i, double* acc) { out[i] = E[i] * acc[0]; });
   };
-  // Kn·[v; w] = P̄v + Āᵀw, handed per row (or long-row chunk) to emit(j, first, value)
-  auto kn_times = [&](const double* v, const double* w, auto emit_row, auto emit_chunk) {
+  // Kn·[v; w] = P̄v + Āᵀw, handed per short row to emit_row(j, P̄v, Āᵀw), per
+  // long-row chunk to emit_chunk(j, first, parts) and per long row to
+  // emit_long(j, P̄v, Āᵀw)
+  auto kn_times = [&](const double* v, const double* w, auto emit_row, auto emit_chunk,
+                      auto emit_long) {
     spmv<2, false, double, double>(
         tm, d.kn, d.kn_ci, d.kn_raw,
         [&](int col, double a, double* acc) {
@@ -961,8 +1072,10 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
           else acc[1] += a * E[col - n] * w[col - n];
         },
         [&](int j, double* acc) { emit_row(j, c * D[j] * acc[0], D[j] * acc[1]); },
-        [&](int j, int first, double* acc) { emit_chunk(j, first, c * D[j] * acc[0], D[j] * acc[1]); });
+        [&](int j, int first, double* acc) { emit_chunk(j, first, c * D[j] * acc[0], D[j] * acc[1]); },
+        [&](int j, double* acc) { emit_long(j, c * D[j] * acc[0], D[j] * acc[1]); });
   };
+  auto no_chunk = [](int, int, double, double) {};
 
   // active sets, zero start, Jacobi diagonal P̄_jj + δ + δ⁻¹Σ_act Ā_ij²
   for (int i = tid; i < m; i += nth) {
@@ -971,12 +1084,7 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
     act[i] = (yi < 0.0 && !(ty & kLInf)) ? 1 : ((yi > 0.0 && !(ty & kUInf)) ? 2 : 0);
     y[i] = 0.0;
   }
-  for (int j = tid; j < n; j += nth) {
-    x[j] = 0.0;
-    dg[j] = 0.0;
-  }
-  zero_long(tm, d.as, t);
-  zero_long(tm, d.kn, r);
+  for (int j = tid; j < n; j += nth) x[j] = 0.0;
   if (!tm.sync()) return false;
   spmv<1, false, double, double>(
       tm, d.kn, d.kn_ci, d.kn_raw,
@@ -986,10 +1094,7 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
           acc[0] += e * e;
         }
       },
-      [&](int j, double* acc) { dg[j] = d.pdiag[j] + delta + idelta * D[j] * D[j] * acc[0]; },
-      [&](int j, int first, double* acc) {
-        atomicAdd(&dg[j], idelta * D[j] * D[j] * acc[0] + (first ? d.pdiag[j] + delta : 0.0));
-      });
+      [&](int j, double* acc) { dg[j] = d.pdiag[j] + delta + idelta * D[j] * D[j] * acc[0]; });
   if (!tm.sync()) return false;
 
   for (int pass = 0; pass <= P.polish_refine; ++pass) {
@@ -1003,14 +1108,11 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
     }
     if (!tm.sync()) return false;
     // rhs = −q̄ − P̄x − Āᵀ(y − r₂/δ) into r
-    kn_times(
-        x, t, [&](int j, double pv, double av) { r[j] = -d.q[j] - pv - av; },
-        [&](int j, int first, double pv, double av) {
-          atomicAdd(&r[j], -pv - av - (first ? d.q[j] : 0.0));
-        });
-    zero_long(tm, d.kn, kp);
+    {
+      auto rhs = [&](int j, double pv, double av) { r[j] = -d.q[j] - pv - av; };
+      kn_times(x, t, rhs, no_chunk, rhs);
+    }
     if (!tm.sync()) return false;
-    zero_long(tm, d.as, t);
     // PCG for the correction Δx from zero
     double red[2] = {0.0, 0.0};  // (r, M⁻¹r), ‖r‖∞
     for (int j = tid; j < n; j += nth) {
@@ -1032,10 +1134,7 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
       spmv<1, false, double, double>(
           tm, d.as, d.a_ci, d.a_raw,
           [&](int col, double a, double* acc) { acc[0] += a * D[col] * p[col]; },
-          [&](int i, double* acc) { t[i] = act[i] ? idelta * E[i] * acc[0] : 0.0; },
-          [&](int i, int, double* acc) {
-            if (act[i]) atomicAdd(&t[i], idelta * E[i] * acc[0]);
-          });
+          [&](int i, double* acc) { t[i] = act[i] ? idelta * E[i] * acc[0] : 0.0; });
       if (!tm.sync()) return false;
       // Kp = P̄p + δp + Āᵀt and pᵀKp = pᵀP̄p + δ‖p‖² + δ‖t‖²
       double g[1] = {0.0};
@@ -1045,10 +1144,10 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
             kp[j] = pv + av + delta * p[j];
             g[0] += p[j] * pv + delta * p[j] * p[j];
           },
-          [&](int j, int first, double pv, double av) {
-            atomicAdd(&kp[j], pv + av + (first ? delta * p[j] : 0.0));
+          [&](int j, int first, double pv, double) {
             g[0] += p[j] * pv + (first ? delta * p[j] * p[j] : 0.0);
-          });
+          },
+          [&](int j, double pv, double av) { kp[j] = pv + av + delta * p[j]; });
       for (int i = tid; i < m; i += nth) g[0] += delta * t[i] * t[i];
       tm.template publish<1, 0u>(g);
       if (!tm.sync()) return false;
@@ -1065,7 +1164,6 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
         red2[0] += rj * zj;
         red2[1] = fmax(red2[1], fabs(rj));
       }
-      zero_long(tm, d.as, t);
       tm.template publish<2, 2u>(red2);
       if (!tm.sync()) return false;
       tm.template collect<2, 2u>(red2);
@@ -1073,26 +1171,19 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
       const double beta_c = red2[0] / rz;
       rz = red2[0];
       for (int j = tid; j < n; j += nth) p[j] = zz[j] + beta_c * p[j];
-      zero_long(tm, d.kn, kp);
       if (!tm.sync()) return false;
     }
     if (!tm.sync()) return false;
     // x ← x + Δx, y ← y + (Ā_act Δx − r₂)/δ
-    zero_long(tm, d.as, t);
-    if (!tm.sync()) return false;
     a_times(dxp, t);
     for (int j = tid; j < n; j += nth) x[j] += dxp[j];
     if (!tm.sync()) return false;
     for (int i = tid; i < m; i += nth)
       if (act[i]) y[i] += (t[i] - r2[i]) * idelta;
-    zero_long(tm, d.as, t);
-    zero_long(tm, d.kn, r);
     if (!tm.sync()) return false;
   }
 
   // acceptance: signs of y on the active rows, unscaled residuals
-  zero_long(tm, d.kn, kp);
-  if (!tm.sync()) return false;
   a_times(x, t);
   double chk[4] = {0.0, 0.0, 0.0, 0.0};  // prim, dual·c, sign violation, c·objective
   kn_times(
@@ -1101,10 +1192,10 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
         kp[j] = pv + av;
         chk[3] += x[j] * (0.5 * pv + d.q[j]);
       },
-      [&](int j, int first, double pv, double av) {
-        atomicAdd(&kp[j], pv + av);
+      [&](int j, int first, double pv, double) {
         chk[3] += x[j] * (0.5 * pv + (first ? d.q[j] : 0.0));
-      });
+      },
+      [&](int j, double pv, double av) { kp[j] = pv + av; });
   if (!tm.sync()) return false;
   for (int i = tid; i < m; i += nth) {
     const double zi = fmin(fmax(t[i], d.l[i]), d.u[i]);
@@ -1139,8 +1230,18 @@ template <class Team, typename T>
 __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   const int n = d.n, m = d.m, tid = tm.tid(), nth = tm.nthreads();
   const double sigma = P.sigma, alpha = P.alpha;
+  const T sigT = T(sigma);
   const double c = d.sc->c;
   double rho_bar = d.sc->rho_bar;
+  // Scalars of the PCG recurrence (γ, α, β, tolerance, and α, β and the stop
+  // flag handed to every thread), updated by warp 0 of each CTA after each
+  // reduction: every CTA derives the same values from the same reduced
+  // inputs, and the narrow FP64 pipe runs the divisions once per CTA rather
+  // than once per warp.
+  double* scal = tm.sm + kScalOff;
+  T* scalT = reinterpret_cast<T*>(scal + 5);
+  int* sflag = reinterpret_cast<int*>(scal + 7);
+  const bool warp0 = (threadIdx.x >> 5) == 0;
   const unsigned long long t_start = gtimer();
   // Pointers read once (restrict-qualified for the compiler).
   const int* __restrict__ kn_ci = d.kn_ci;
@@ -1172,7 +1273,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   const double* __restrict__ rho_inv = d.rho_inv;
 
   int status = kUnsolved, k = 0, pcg_total = 0, rho_updates = 0, checks = 0;
-  bool dinv_dirty = false;
   // PCG tolerance before this solve's first check: the scaled residuals of
   // the current iterates (a warm start) — those of the last check, or, when
   // the data changed since (marked −1), recomputed below — else a fraction
@@ -1190,14 +1290,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     dzt[i] = T(0);
   }
   for (int j = tid; j < n; j += nth) dxt[j] = T(0);
-  zero_long(tm, d.kn, rbuf(cur));
-  zero_long(tm, d.kn, bv);
-  zero_long(tm, d.as, tbuf(cur));
-  if (stale) {
-    zero_long(tm, d.kn, d.px);
-    zero_long(tm, d.kn, d.aty);
-    zero_long(tm, d.as, d.ax);
-  }
   if (!tm.sync()) return false;
   if (stale) {
     // ‖Āx̄ − z̄‖∞ and ‖P̄x̄ + q̄ + Āᵀȳ‖∞ on the current iterates (§5.1, scaled)
@@ -1211,15 +1303,10 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         [&](int j, double* acc) {
           d.px[j] = acc[0];
           d.aty[j] = acc[1];
-        },
-        [&](int j, int, double* acc) {
-          atomicAdd(&d.px[j], acc[0]);
-          atomicAdd(&d.aty[j], acc[1]);
         });
     spmv<1, false, double, T>(
         tm, d.as, a_ci, a_v, [&](int col, T v, double* acc) { acc[0] += (double)v * x[col]; },
-        [&](int i, double* acc) { d.ax[i] = acc[0]; },
-        [&](int i, int, double* acc) { atomicAdd(&d.ax[i], acc[0]); });
+        [&](int i, double* acc) { d.ax[i] = acc[0]; });
     if (!tm.sync()) return false;
     double res[2] = {0.0, 0.0};
     for (int i = tid; i < m; i += nth) res[0] = fmax(res[0], fabs(d.ax[i] - z[i]));
@@ -1238,10 +1325,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     // from FP64 vectors with FP64 accumulation in both modes, so that in the
     // FP32 mode every ADMM iteration restarts PCG from an accurate residual
     // (mixed-precision iterative refinement of the linear solve).
-    if (dinv_dirty) {
-      for (int j = tid; j < n; j += nth) dinv[j] = T(1.0 / d.dg[j]);
-      dinv_dirty = false;
-    }
     {
       T* __restrict__ r = rbuf(cur);
       spmv<2, false, double, T>(
@@ -1259,12 +1342,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
             const double bj = sigma * x[j] - d.q[j];
             r[j] = T(bj - sigma * xt[j] + acc[0]);
             bv[j] = T(bj + acc[1]);
-          },
-          [&](int j, int first, double* acc) {
-            const double bj = first ? sigma * x[j] - d.q[j] : 0.0;
-            const double xs = first ? sigma * xt[j] : 0.0;
-            atomicAdd(&r[j], T(bj - xs + acc[0]));
-            atomicAdd(&bv[j], T(bj + acc[1]));
           });
     }
     if (!tm.sync()) return false;
@@ -1295,51 +1372,61 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       spmv<1, false, T, T>(
           tm, d.as, a_ci, a_v,
           [&](int col, T v, T* acc) { acc[0] += v * (r[col] * dinv[col]); },
-          [&](int i, T* acc) { t[i] = rhoT[i] * acc[0]; },
-          [&](int i, int, T* acc) { atomicAdd(&t[i], rhoT[i] * acc[0]); });
-      zero_long(tm, d.kn, wbuf(cur));
+          [&](int i, T* acc) { t[i] = rhoT[i] * acc[0]; });
     }
     tm.template publish<3, 6u>(red3t);
     if (!tm.sync()) return false;
     tm.template collect<3, 6u>(red3);
-    double gamma = red3[0];
-    const double bnorm = red3[2];
-    // PCG accuracy (reading of "up to some predefined accuracy", §3.1).
-    const double tol = fmax(fmax(P.pcg_floor * bnorm, P.pcg_reduce * red3[1]),
-                            have_check ? P.pcg_kappa * fmin(rp_bar, rd_bar) : 0.1 * P.pcg_kappa * bnorm);
-    bool done = !(red3[1] > tol);
-    double alpha_c = 0.0, beta_c = 0.0;
+    if (warp0) {
+      // PCG accuracy (reading of "up to some predefined accuracy", §3.1).
+      const double bnorm = red3[2];
+      const double tol = fmax(fmax(P.pcg_floor * bnorm, P.pcg_reduce * red3[1]),
+                              have_check ? P.pcg_kappa * fmin(rp_bar, rd_bar)
+                                         : 0.1 * P.pcg_kappa * bnorm);
+      scal[0] = red3[0];  // γ = (r, M⁻¹r)
+      scal[3] = tol;
+      if (threadIdx.x == 0) *sflag = !(red3[1] > tol);
+    }
+    __syncthreads();
+    bool done = *sflag != 0;
     if (!done) {
       // --- W: w = Ku, (w,u)
       double red1[1] = {0.0};
       T wacc = T(0);
       T* __restrict__ w = wbuf(cur);
       const T* __restrict__ tg = tbuf(cur);
+      // long rows of w stay as chunk partials: P1, the only reader, sums them
       spmv<1, false, T, T>(
           tm, d.kn, kn_ci, kn_v,
           [&](int col, T v, T* acc) { acc[0] += v * (col < n ? u[col] : tg[col - n]); },
           [&](int j, T* acc) {
-            const T wj = T(sigma) * u[j] + acc[0];
+            const T wj = sigT * u[j] + acc[0];
             w[j] = wj;
             wacc += wj * u[j];
           },
           [&](int j, int first, T* acc) {
-            const T part = acc[0] + (first ? T(sigma) * u[j] : T(0));
-            atomicAdd(&w[j], part);
-            wacc += part * u[j];
-          });
+            wacc += (acc[0] + (first ? sigT * u[j] : T(0))) * u[j];
+          },
+          NoLong{}, LazyTag{});
       const T red1t[1] = {wacc};
       tm.template publish<1, 0u>(red1t);
       if (!tm.sync()) return false;
       tm.template collect<1, 0u>(red1);
-      if (red1[0] > 0.0) alpha_c = gamma / red1[0];
-      else done = true;
+      if (warp0) {
+        const double a = red1[0] > 0.0 ? scal[0] / red1[0] : 0.0;
+        scal[1] = a;
+        scalT[0] = T(a);
+        scalT[1] = T(0);
+        if (threadIdx.x == 0) *sflag = !(red1[0] > 0.0);
+      }
+      __syncthreads();
+      done = *sflag != 0;
     }
     int j_it = 0;
     while (!done) {
       const int nxt = cur ^ 1;
       const bool first = j_it == 0;
-      const T aT = T(alpha_c), bT = T(beta_c);
+      const T aT = scalT[0], bT = scalT[1];
       // --- P1: p = u + βp, s = w + βs, x̃ += αp, r −= αs, u = M⁻¹r,
       //         Āp = t/ρ + β·Āp, z̃ += α·Āp   (elementwise)
       {
@@ -1349,9 +1436,13 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         T* __restrict__ rn = rbuf(nxt);
         T* __restrict__ sn = sbuf(nxt);
         const T* __restrict__ tc = tbuf(cur);
+        const bool lazy_w = d.kn.nlong > 0;
         for (int j = tid; j < n; j += nth) {
+          T wj;  // w = Ku, its long rows summed here from the product's partials
+          if (lazy_w && d.kn.lidx[j] >= 0) wj = sigT * u[j] + long_sum<T>(d.kn, d.kn.lidx[j], 0);
+          else wj = wc[j];
           const T pj = first ? u[j] : u[j] + bT * pv[j];
-          const T sj = first ? wc[j] : wc[j] + bT * sc[j];
+          const T sj = first ? wj : wj + bT * sc[j];
           pv[j] = pj;
           sn[j] = sj;
           dxt[j] += aT * pj;
@@ -1365,7 +1456,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           ap[i] = api;
           dzt[i] += aT * api;
         }
-        zero_long(tm, d.kn, wbuf(nxt));
       }
       if (!tm.sync()) return false;
       // --- P1b: t' = RĀu
@@ -1373,8 +1463,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         T* __restrict__ tn = tbuf(nxt);
         spmv<1, false, T, T>(
             tm, d.as, a_ci, a_v, [&](int col, T v, T* acc) { acc[0] += v * u[col]; },
-            [&](int i, T* acc) { tn[i] = rhoT[i] * acc[0]; },
-            [&](int i, int, T* acc) { atomicAdd(&tn[i], rhoT[i] * acc[0]); });
+            [&](int i, T* acc) { tn[i] = rhoT[i] * acc[0]; });
       }
       if (!tm.sync()) return false;
       ++j_it;
@@ -1396,16 +1485,14 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
             tm, d.kn, kn_ci, kn_v,
             [&](int col, T v, T* acc) { acc[0] += v * (col < n ? u[col] : tg[col - n]); },
             [&](int j, T* acc) {
-              const T wj = T(sigma) * u[j] + acc[0];
+              const T wj = sigT * u[j] + acc[0];
               wn[j] = wj;
               g1 += wj * u[j];
             },
             [&](int j, int first2, T* acc) {
-              const T part = acc[0] + (first2 ? T(sigma) * u[j] : T(0));
-              atomicAdd(&wn[j], part);
-              g1 += part * u[j];
-            });
-        zero_long(tm, d.as, tbuf(cur));
+              g1 += (acc[0] + (first2 ? sigT * u[j] : T(0))) * u[j];
+            },
+            NoLong{}, LazyTag{});
         red2t[0] = g0;
         red2t[1] = g1;
         red2t[2] = g2;
@@ -1414,14 +1501,29 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       if (!tm.sync()) return false;
       tm.template collect<3, 4u>(red2);
       cur = nxt;
-      if (!(red2[2] > tol) || j_it >= P.pcg_max_iter) break;
-      const double gamma_n = red2[0];
-      const double beta_n = gamma_n / gamma;
-      const double denom = red2[1] - beta_n * gamma_n / alpha_c;
-      if (!(denom > 0.0) || !(gamma_n > 0.0)) break;  // breakdown: p vanished
-      beta_c = beta_n;
-      alpha_c = gamma_n / denom;
-      gamma = gamma_n;
+      if (warp0) {
+        // Chronopoulos–Gear update: β = γ'/γ, α = γ'/((w,u) − βγ'/α); stop
+        // at the tolerance, the iteration cap, or a breakdown (p vanished)
+        int stop = !(red2[2] > scal[3]) || j_it >= P.pcg_max_iter;
+        if (!stop) {
+          const double gamma_n = red2[0];
+          const double beta_n = gamma_n / scal[0];
+          const double denom = red2[1] - beta_n * gamma_n / scal[1];
+          if (!(denom > 0.0) || !(gamma_n > 0.0)) {
+            stop = 1;
+          } else {
+            const double a = gamma_n / denom;
+            scal[0] = gamma_n;
+            scal[1] = a;
+            scal[2] = beta_n;
+            scalT[0] = T(a);
+            scalT[1] = T(beta_n);
+          }
+        }
+        if (threadIdx.x == 0) *sflag = stop;
+      }
+      __syncthreads();
+      if (*sflag) break;
     }
 
     // --- U: Algorithm 1 steps 5–7, y in the form ρ(v − Π(v)) of Eq. (zy-update)
@@ -1447,19 +1549,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       wm[i] = rh * zn - yn;
       um[i] = rh * (zn - zti) - yn;
     }
-    zero_long(tm, d.kn, rbuf(cur));
-    zero_long(tm, d.kn, bv);
-    zero_long(tm, d.as, tbuf(cur));
     const bool check = (k % P.check_interval == 0) || (k == P.max_iter);
-    if (check) {
-      zero_long(tm, d.kn, d.px);
-      zero_long(tm, d.kn, d.aty);
-      zero_long(tm, d.kn, d.pdx);
-      zero_long(tm, d.kn, d.atdy);
-      zero_long(tm, d.as, d.ax);
-      zero_long(tm, d.as, d.adx);
-      zero_long(tm, d.as, d.azt);
-    }
     if (!tm.sync()) return false;
     if (!check) continue;
 
@@ -1490,12 +1580,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
             d.aty[j] = acc[1];
             d.pdx[j] = acc[2];
             d.atdy[j] = acc[3];
-          },
-          [&](int j, int, double* acc) {
-            atomicAdd(&d.px[j], acc[0]);
-            atomicAdd(&d.aty[j], acc[1]);
-            atomicAdd(&d.pdx[j], acc[2]);
-            atomicAdd(&d.atdy[j], acc[3]);
           });
       spmv<3, false, double, T>(
           tm, d.as, a_ci, a_v,
@@ -1509,11 +1593,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
             d.ax[i] = acc[0];
             d.adx[i] = acc[1];
             d.azt[i] = acc[2];
-          },
-          [&](int i, int, double* acc) {
-            atomicAdd(&d.ax[i], acc[0]);
-            atomicAdd(&d.adx[i], acc[1]);
-            atomicAdd(&d.azt[i], acc[2]);
           });
     }
     if (!tm.sync()) return false;
@@ -1567,7 +1646,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       R[22] += qj * x[j];
     }
     if (threadIdx.x == 0) R[23] = (double)(gtimer() - t_start);
-    zero_long(tm, d.kn, d.dg);
     tm.template publish<24, kMaxMask>(R);
     if (!tm.sync()) return false;
     tm.template collect<24, kMaxMask>(R);
@@ -1617,7 +1695,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         }
         jacobi_rows(tm, d, sigma, rho_bar);
         if (!tm.sync()) return false;
-        dinv_dirty = true;
       }
     }
   }
@@ -1656,10 +1733,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     sc->prim_res = prim_res;
     sc->dual_res = dual_res;
   }
-  // A pending Jacobi rebuild (ρ̄ changed at the last check) is applied now so
-  // that a warm-started solve sees a consistent preconditioner.
-  if (dinv_dirty)
-    for (int j = tid; j < n; j += nth) dinv[j] = T(1.0 / d.dg[j]);
   return true;
 }
 

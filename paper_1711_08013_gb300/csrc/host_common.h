@@ -29,9 +29,11 @@ struct SchedHost {
   int group = 1, long_thresh = 256, npos = 0;
   std::vector<int2> slices;
   std::vector<int> srow;
-  std::vector<int4> chunks;
+  std::vector<int4> chunks;  // (row, begin, end, long-row index)
   std::vector<int> long_rows;
-  std::vector<int> pos;  // CSR index → position in the sliced layout
+  std::vector<int2> lrange;  // per long row: (first chunk, number of chunks)
+  std::vector<int> lidx;     // per row: long-row index, −1 for a short row
+  std::vector<int> pos;      // CSR index → position in the sliced layout
 };
 
 inline int sched_group(double mean_short, long long nshort, long long nwarps) {
@@ -68,6 +70,7 @@ inline SchedHost make_sched(const std::vector<int>& rp, long long nwarps) {
   std::stable_sort(shortr.begin(), shortr.end(),
                    [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
   S.pos.assign(nnz, -1);
+  S.lidx.assign(nrows, -1);
   const int nsl = (int)((scount + spw - 1) / spw);
   S.srow.assign((size_t)nsl * spw, -1);
   int p = 0;
@@ -86,11 +89,15 @@ inline SchedHost make_sched(const std::vector<int>& rp, long long nwarps) {
     }
     p += 32 * W;
   }
-  for (int r : S.long_rows) {
+  for (int lr = 0; lr < (int)S.long_rows.size(); ++lr) {
+    const int r = S.long_rows[lr];
+    const int c0 = (int)S.chunks.size();
     for (int b = rp[r]; b < rp[r + 1]; b += kChunk) {
       const int e = std::min(b + kChunk, rp[r + 1]);
-      S.chunks.push_back(make_int4(r, p + (b - rp[r]), p + (e - rp[r]), b == rp[r] ? 1 : 0));
+      S.chunks.push_back(make_int4(r, p + (b - rp[r]), p + (e - rp[r]), lr));
     }
+    S.lrange.push_back(make_int2(c0, (int)S.chunks.size() - c0));
+    S.lidx[r] = lr;
     for (int k = rp[r]; k < rp[r + 1]; ++k) S.pos[k] = p + (k - rp[r]);
     p += rp[r + 1] - rp[r];
   }

@@ -39,7 +39,8 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-enum : int { kNaOk = 0, kNaBadCsc = 1, kNaLongRow = 2, kNaNoRoom = 3 };
+enum : int { kNaOk = 0, kNaBadCsc = 1, kNaLongRow = 2, kNaNoRoom = 3, kNaNonFinite = 4,
+             kNaLgtU = 5 };
 
 struct NaInput {
   int n, m, nnzP, nnzA;
@@ -80,6 +81,10 @@ struct NaSched {
   int* long_rows;
   int* lpos;      // first position of each long row
   int* order;     // short rows, stably sorted by decreasing length
+  int2* lrange;   // per long row: first chunk, number of chunks
+  int* lidx;      // per row: long-row index, −1 for a short row
+  double* cpart;  // per chunk: partial values of a product
+  unsigned* ccount;  // per long row: chunks stored (zeroed by the build)
 };
 
 template <typename T>
@@ -106,7 +111,7 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   const size_t ch_kn = nkn / kChunk + nkn / 257 + 1, lr_kn = nkn / 257 + 1;
   const size_t ch_a = na / kChunk + na / 257 + 1, lr_a = na / 257 + 1;
   const size_t nr = n > m ? n : m;
-  constexpr int kSlots = 96;  // ≥ the number of take() calls below (93)
+  constexpr int kSlots = 104;  // ≥ the number of take() calls below (101)
   size_t o[kSlots];
   int c = 0;
   o[c++] = L.template take<int>(n + 1);       // 0 kn rp
@@ -138,6 +143,15 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   o[c++] = L.template take<int>(kMaxBins + 2);  // 26 bin starts
   o[c++] = L.template take<int>(nr + 2);      // 27 slice widths / starts
   o[c++] = L.template take<uint8_t>(m);       // 28 rtype
+  const int at_lr = c;
+  o[c++] = L.template take<int2>(lr_kn);      // kn long-row chunk ranges
+  o[c++] = L.template take<double>(ch_kn * kMaxNV);  // kn chunk partials
+  o[c++] = L.template take<unsigned>(lr_kn);  // kn long-row counters
+  o[c++] = L.template take<int2>(lr_a);       // a long-row chunk ranges
+  o[c++] = L.template take<double>(ch_a * kMaxNV);   // a chunk partials
+  o[c++] = L.template take<unsigned>(lr_a);   // a long-row counters
+  o[c++] = L.template take<int>(n);           // kn row → long-row index
+  o[c++] = L.template take<int>(m);           // a row → long-row index
   const int at_pact = c;
   o[c++] = L.template take<uint8_t>(m);       // 29 polishing row states
   const int nvec_n = 22, nvec_m = 22;
@@ -153,17 +167,21 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   o[c++] = L.template take<Scalars>(1);
   const int at_err = c;
   o[c++] = L.template take<int>(2);
-  static_assert(30 + 22 + 22 + 11 + 6 + 2 <= kSlots, "scratch slot table too small");
+  static_assert(38 + 22 + 22 + 11 + 6 + 2 <= kSlots, "scratch slot table too small");
   if (base && p) {
     Dev<T>& d = p->d;
     d.n = in.n;
     d.m = in.m;
     p->kn = NaSched{(int*)(base + o[0]),   (int*)(base + o[1]),   (double*)(base + o[2]),
                     (int2*)(base + o[18]), (int*)(base + o[19]),  (int4*)(base + o[12]),
-                    (int*)(base + o[13]),  (int*)(base + o[14]),  (int*)(base + o[20])};
+                    (int*)(base + o[13]),  (int*)(base + o[14]),  (int*)(base + o[20]),
+                    (int2*)(base + o[at_lr]), (int*)(base + o[at_lr + 6]),
+                    (double*)(base + o[at_lr + 1]), (unsigned*)(base + o[at_lr + 2])};
     p->a = NaSched{(int*)(base + o[3]),   (int*)(base + o[4]),   (double*)(base + o[5]),
                    (int2*)(base + o[21]), (int*)(base + o[22]),  (int4*)(base + o[15]),
-                   (int*)(base + o[16]),  (int*)(base + o[17]),  (int*)(base + o[23])};
+                   (int*)(base + o[16]),  (int*)(base + o[17]),  (int*)(base + o[23]),
+                   (int2*)(base + o[at_lr + 3]), (int*)(base + o[at_lr + 7]),
+                   (double*)(base + o[at_lr + 4]), (unsigned*)(base + o[at_lr + 5])};
     p->tmp_ci = (int*)(base + o[6]);
     p->tmp_raw = (double*)(base + o[7]);
     p->plen = (int*)(base + o[8]);
@@ -340,6 +358,8 @@ __device__ bool build_sliced(Sched& S, const NaSched& B, NaPtrs<T>& sp, int nrow
   for (int q = tid; q < nsl; q += nth)
     B.slices[q] = make_int2(sp.wsum[q], (sp.wsum[q + 1] - sp.wsum[q]) / 32);
   for (int q = tid; q < nsl * spw; q += nth) B.srow[q] = q < nshort ? B.order[q] : -1;
+  for (int r = tid; r < nrows; r += nth) B.lidx[r] = -1;
+  __syncthreads();
   // long rows in row order after the slices, with their chunks (few long
   // rows: one thread), then the sliced arrays
   if (tid == 0) {
@@ -349,9 +369,13 @@ __device__ bool build_sliced(Sched& S, const NaSched& B, NaPtrs<T>& sp, int nrow
       if (e - b <= thresh) continue;
       B.long_rows[nl] = r;
       B.lpos[nl] = p;
-      ++nl;
+      B.ccount[nl] = 0u;
+      B.lidx[r] = nl;
+      const int c0 = nc;
       for (int k = b; k < e; k += kChunk)
-        B.chunks[nc++] = make_int4(r, p + (k - b), p + (min(k + kChunk, e) - b), k == b);
+        B.chunks[nc++] = make_int4(r, p + (k - b), p + (min(k + kChunk, e) - b), nl);
+      B.lrange[nl] = make_int2(c0, nc - c0);
+      ++nl;
       p += e - b;
     }
     const size_t np = p;
@@ -379,6 +403,10 @@ __device__ bool build_sliced(Sched& S, const NaSched& B, NaPtrs<T>& sp, int nrow
       S.srow = B.srow;
       S.chunks = B.chunks;
       S.long_rows = B.long_rows;
+      S.lrange = B.lrange;
+      S.lidx = B.lidx;
+      S.cpart = B.cpart;
+      S.ccount = B.ccount;
       S.prefetch = 0;
     }
   }
@@ -468,6 +496,31 @@ __global__ void __launch_bounds__(kThreads) k_noalloc(NaInput in, const __grid_c
     if (tid == 0) d.sc->dev_error = sp.err[0];
     return;
   }
+  // --- values, as osqp_setup checks them: P, A and q finite, l and u not
+  // NaN, l ≤ u (bit 0: a non-finite value, bit 1: some l_i > u_i; the
+  // non-finite report takes precedence, as on the host)
+  if (tid == 0) *sp.flag = 0;
+  __syncthreads();
+  {
+    int bad = 0;
+    for (int k = tid; k < in.nnzP; k += nth)
+      if (!isfinite(in.Px[k])) bad |= 1;
+    for (int k = tid; k < in.nnzA; k += nth)
+      if (!isfinite(in.Ax[k])) bad |= 1;
+    for (int j = tid; j < n; j += nth)
+      if (!isfinite(in.q[j])) bad |= 1;
+    for (int i = tid; i < m; i += nth) {
+      const double lo = in.l[i], hi = in.u[i];
+      if (isnan(lo) || isnan(hi)) bad |= 1;
+      else if (lo > hi) bad |= 2;
+    }
+    if (bad) atomicOr(sp.flag, bad);
+  }
+  __syncthreads();
+  if (*(volatile int*)sp.flag != 0) {
+    if (tid == 0) d.sc->dev_error = (*sp.flag & 1) ? kNaNonFinite : kNaLgtU;
+    return;
+  }
   // --- Kn = [P̄ Āᵀ] rows: full-P part by counting + atomic scatter + rank sort
   for (int k = tid; k < in.nnzP; k += nth) {
     const int j = col_of(in.Pp, n, k), i = in.Pi[k];
@@ -480,7 +533,7 @@ __global__ void __launch_bounds__(kThreads) k_noalloc(NaInput in, const __grid_c
   block_exclusive_scan(sp.cur_n, sp.kn.rp, n, sh_int);
   for (int j = tid; j < n; j += nth) {
     sp.cur_n[j] = sp.kn.rp[j];
-    if (sp.plen[j] > kNoallocMaxRow) atomicExch(sp.err, kNaLongRow);
+    if (sp.kn.rp[j + 1] - sp.kn.rp[j] > kNoallocMaxRow) atomicExch(sp.err, kNaLongRow);
   }
   __syncthreads();
   for (int k = tid; k < in.nnzP; k += nth) {
@@ -593,6 +646,8 @@ int read_info(const NaInput& in, int precision, char* base, cudaStream_t st, osq
   if (cudaStreamSynchronize(st) != cudaSuccess) return OSQP_ERR_CUDA;
   if (sc.dev_error == kNaBadCsc) return OSQP_ERR_CSC;
   if (sc.dev_error == kNaLongRow || sc.dev_error == kNaNoRoom) return OSQP_ERR_LIMIT;
+  if (sc.dev_error == kNaNonFinite) return OSQP_ERR_NONFINITE;
+  if (sc.dev_error == kNaLgtU) return OSQP_ERR_LGTU;
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->status = sc.status;
@@ -672,7 +727,7 @@ extern "C" int32_t osqp_solve_noalloc(int32_t n, int32_t m, const int32_t* P_col
   P.scaling_iters = s.scaling_iters;
   P.max_rho_updates = s.max_rho_updates;
   P.pcg_max_iter = s.pcg_max_iter;
-  P.barrier_timeout_ns = 2000000000ull;
+  P.barrier_timeout_ns = 0;  // the one-CTA team waits on no grid or cluster barrier
   P.polish = s.polish;
   P.polish_refine = s.polish_refine_iter;
   P.delta = s.delta;

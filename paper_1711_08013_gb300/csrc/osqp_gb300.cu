@@ -151,7 +151,7 @@ __global__ void k_warm_xy(const __grid_constant__ Dev<T> d, const double* __rest
   }
 }
 
-// warm start, part 2: z̄ = z̃ = Āx̄ (long rows of z̄, z̃ were zeroed in part 1)
+// warm start, part 2: z̄ = z̃ = Āx̄
 template <typename T>
 __global__ void k_warm_z(const __grid_constant__ Dev<T> d) {
   PlainTeam tm;
@@ -160,10 +160,6 @@ __global__ void k_warm_z(const __grid_constant__ Dev<T> d) {
       [&](int i, double* acc) {
         d.z[i] = acc[0];
         d.zt[i] = acc[0];
-      },
-      [&](int i, int, double* acc) {
-        atomicAdd(&d.z[i], acc[0]);
-        atomicAdd(&d.zt[i], acc[0]);
       });
 }
 
@@ -245,6 +241,10 @@ void take_sched(Arena& A, const SchedHost& h, int nrows, Sched& S) {
   S.srow = A.take<int>(h.srow.size());
   S.chunks = A.take<int4>(h.chunks.size());
   S.long_rows = A.take<int>(h.long_rows.size());
+  S.lrange = A.take<int2>(h.lrange.size());
+  S.lidx = A.take<int>(h.lidx.size());
+  S.cpart = A.take<double>(h.chunks.size() * kMaxNV);
+  S.ccount = A.take<unsigned>(h.lrange.size());
   S.prefetch = 0;  // one problem's data stay in L2
 }
 
@@ -533,6 +533,10 @@ int carve_and_upload(osqp_solver* s, size_t part_doubles) {
     CK(up((void*)S.srow, h.srow.data(), h.srow.size() * sizeof(int)));
     CK(up((void*)S.chunks, h.chunks.data(), h.chunks.size() * sizeof(int4)));
     CK(up((void*)S.long_rows, h.long_rows.data(), h.long_rows.size() * sizeof(int)));
+    CK(up((void*)S.lrange, h.lrange.data(), h.lrange.size() * sizeof(int2)));
+    CK(up((void*)S.lidx, h.lidx.data(), h.lidx.size() * sizeof(int)));
+    if (!h.lrange.empty())
+      CK(cudaMemsetAsync(S.ccount, 0, h.lrange.size() * sizeof(unsigned), s->stream));
   }
   CK(cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->stream));
   return OSQP_OK;
@@ -904,6 +908,22 @@ int32_t osqp_get_certificate(osqp_solver* s, double* py, double* dx) {
   return OSQP_OK;
 }
 
+int32_t osqp_diag_scaling(osqp_solver* s, double* D, double* E, double* c, double* jacobi) {
+  if (!s) return OSQP_ERR_ARG;
+  const bool f64 = s->set.precision == OSQP_PRECISION_FP64;
+  const double* Dd = f64 ? s->d64.D : s->d32.D;
+  const double* Ed = f64 ? s->d64.E : s->d32.E;
+  const double* gd = f64 ? s->d64.dg : s->d32.dg;
+  if (D) CK(cudaMemcpyAsync(D, Dd, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+  if (E && s->m)
+    CK(cudaMemcpyAsync(E, Ed, sizeof(double) * s->m, cudaMemcpyDeviceToHost, s->stream));
+  if (jacobi)
+    CK(cudaMemcpyAsync(jacobi, gd, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+  if (c) CK(cudaMemcpyAsync(c, &s->sc->c, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return OSQP_OK;
+}
+
 int32_t osqp_diag_barrier_timeout(double timeout_s) {
   if (!(timeout_s > 0.0) || !(timeout_s <= 10.0)) return OSQP_ERR_ARG;
   constexpr int kBlocks = 4;
@@ -955,7 +975,7 @@ int32_t osqp_diag_sliced_layout(int32_t nrows, const int32_t* rowptr, int64_t nw
       chunks[4 * c + 0] = S.chunks[c].x;
       chunks[4 * c + 1] = S.chunks[c].y;
       chunks[4 * c + 2] = S.chunks[c].z;
-      chunks[4 * c + 3] = S.chunks[c].w;
+      chunks[4 * c + 3] = S.lrange[S.chunks[c].w].x == (int)c ? 1 : 0;
     }
   return OSQP_OK;
 }

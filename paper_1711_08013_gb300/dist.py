@@ -75,3 +75,50 @@ def gather_objects(obj):
     out = [None] * dist.get_world_size()
     dist.all_gather_object(out, obj)
     return out
+
+
+class ShardedBatch:
+    """One set of independent problems partitioned across ranks.
+
+    Every rank holds the same list of work estimates (one per problem of the
+    global set); lpt_partition assigns each problem to one rank, each rank
+    generates and solves only its share on its own GPU, and results are
+    combined on the host on request.  make_problem(i) builds global problem
+    i; make_solver(problems) returns an object with solve(), result(k) (the
+    k-th local problem) and close() — the batched GPU solver in the product
+    path.  No collective touches the data path: the gather moves host
+    objects after the solve."""
+
+    def __init__(self, weights, make_problem, make_solver, rank: int | None = None,
+                 world: int | None = None):
+        if rank is None or world is None:
+            ws, rk, _ = env()
+            world = ws if world is None else world
+            rank = rk if rank is None else rank
+        self.rank, self.world = rank, world
+        self.index = shard(weights, rank, world)
+        self.problems = [make_problem(i) for i in self.index]
+        self.solver = make_solver(self.problems) if self.problems else None
+
+    def solve(self):
+        if self.solver is not None:
+            self.solver.solve()
+
+    def local_results(self):
+        """{global index: result} of this rank's problems."""
+        if self.solver is None:
+            return {}
+        return {i: self.solver.result(k) for k, i in enumerate(self.index)}
+
+    def gather(self, pick=lambda r: r):
+        """{global index: pick(result)} of every rank's problems, on every
+        rank (pick keeps the host objects small: e.g. status and x)."""
+        merged = {}
+        for part in gather_objects({i: pick(r) for i, r in self.local_results().items()}):
+            merged.update(part)
+        return merged
+
+    def close(self):
+        if self.solver is not None:
+            self.solver.close()
+            self.solver = None

@@ -41,6 +41,7 @@ class Step:
     pcg_iters: int
     solve_time: float      # device seconds of the solve
     wall: float            # host seconds of update + solve + result read-back
+    z: np.ndarray | None = None
 
 
 class GpuSession:
@@ -65,7 +66,7 @@ class GpuSession:
             self.solver.warm_start(np.zeros(self.n), np.zeros(self.m))
         r = self.solver.solve()
         return Step(r.x, r.y, r.status, r.iter, r.pcg_iters, r.solve_time,
-                    time.perf_counter() - t0)
+                    time.perf_counter() - t0, r.z)
 
     def close(self):
         self.solver.close()

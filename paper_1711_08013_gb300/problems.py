@@ -208,13 +208,30 @@ def mpc_paper(nx: int, T: int = 10, seed: int = 0) -> QP:
                terminal="dare")
 
 
-def mpc_batch(count: int = 4096, seed: int = 3000, nx_range=(4, 32), T_range=(10, 30)) -> list[QP]:
-    """Batched ragged MPC workload: problem i draws nx ~ U{4..32},
-    T ~ U{10..30} from seed `seed`, then is generated with seed `seed`+1+i."""
+def mpc_batch_spec(count: int = 4096, seed: int = 3000, nx_range=(4, 32),
+                   T_range=(10, 30)) -> list[tuple[int, int, int]]:
+    """(nx, T, seed) of every problem of the batched ragged MPC workload:
+    nx ~ U{4..32} and T ~ U{10..30} drawn from seed `seed`, problem i then
+    generated with seed `seed`+1+i (so any subset can be generated alone)."""
     rng = np.random.default_rng(seed)
     nxs = rng.integers(nx_range[0], nx_range[1] + 1, size=count)
     Ts = rng.integers(T_range[0], T_range[1] + 1, size=count)
-    return [mpc(int(nxs[i]), int(Ts[i]), seed=seed + 1 + i) for i in range(count)]
+    return [(int(nxs[i]), int(Ts[i]), seed + 1 + i) for i in range(count)]
+
+
+def mpc_spec_work(nx: int, T: int) -> float:
+    """Estimated matrix entries of one batched MPC problem (dense dynamics
+    blocks, identity couplings and boxes): the weight by which problems are
+    ordered and sharded before they are generated."""
+    nu = nx // 2
+    n = nx * (T + 1) + nu * T
+    return float(T * nx * (nx + nu + 1) + nx + 2 * n)
+
+
+def mpc_batch(count: int = 4096, seed: int = 3000, nx_range=(4, 32), T_range=(10, 30)) -> list[QP]:
+    """Batched ragged MPC workload: problem i draws nx ~ U{4..32},
+    T ~ U{10..30} from seed `seed`, then is generated with seed `seed`+1+i."""
+    return [mpc(nx, T, seed=sd) for nx, T, sd in mpc_batch_spec(count, seed, nx_range, T_range)]
 
 
 # ----------------------------------------------------------------------------

@@ -57,6 +57,10 @@ class Solver:
     def certificate(self):
         return B.osqp_get_certificate(self.handle, self.n, self.m)
 
+    def scaling(self):
+        """(D, E, c, Jacobi diagonal) as held on the device."""
+        return B.osqp_diag_scaling(self.handle, self.n, self.m)
+
     def update_vectors(self, q=None, l=None, u=None):
         B.osqp_update_vectors(self.handle, _sized("q", q, self.n), _sized("l", l, self.m),
                               _sized("u", u, self.m))

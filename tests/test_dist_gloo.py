@@ -72,6 +72,64 @@ def _worker(rank, world, port, out_dir):
     dist.destroy_process_group()
 
 
+class _OracleBatch:
+    """CPU stand-in for the batched GPU solver (same solve/result/close
+    interface), so the sharding and gather of the product path run here."""
+
+    def __init__(self, qps):
+        self.qps = qps
+        self.res = None
+
+    def solve(self):
+        from oracle import oracle as O
+        self.res = [O.solve(q) for q in self.qps]
+
+    def result(self, k):
+        return self.res[k]
+
+    def close(self):
+        self.res = None
+
+
+def _sharded_worker(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    D.init("gloo")
+    spec = pb.mpc_batch_spec(12, seed=3500, nx_range=(3, 6), T_range=(4, 8))
+    weights = [pb.mpc_spec_work(nx, T) for nx, T, _ in spec]
+    sb = D.ShardedBatch(weights, lambda i: pb.mpc(spec[i][0], spec[i][1], seed=spec[i][2]),
+                        _OracleBatch)
+    sb.solve()
+    merged = sb.gather(lambda r: (r.status, r.x.tolist()))
+    with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+        f.write(" ".join(map(str, sb.index)) + "\n")
+    if rank == 0:
+        np.save(os.path.join(out_dir, "sharded.npy"),
+                np.array([merged[i][1] for i in range(len(spec))], dtype=object),
+                allow_pickle=True)
+    sb.close()
+    import torch.distributed as dist
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_sharded_batch_product_path(tmp_path, oracle_mod):
+    """The sharding object that bench.py uses for the batched workload: two
+    ranks split one 12-problem set by LPT on the generator's work estimates,
+    each builds and solves only its share (the batched solver replaced by
+    the oracle on CPU), and the gathered results equal a single-process
+    solve of the whole set; the two shares are disjoint and cover it."""
+    port = _free_port()
+    mp.spawn(_sharded_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    shares = [list(map(int, open(tmp_path / f"rank{r}.txt").read().split())) for r in range(2)]
+    assert sorted(shares[0] + shares[1]) == list(range(12)) and shares[0] and shares[1]
+    merged = np.load(tmp_path / "sharded.npy", allow_pickle=True)
+    spec = pb.mpc_batch_spec(12, seed=3500, nx_range=(3, 6), T_range=(4, 8))
+    for i, (nx, T, sd) in enumerate(spec):
+        ref = oracle_mod.solve(pb.mpc(nx, T, seed=sd)).x
+        assert np.array_equal(np.asarray(merged[i]), ref)
+
+
 def test_two_rank_sharded_solve(tmp_path, oracle_mod):
     port = _free_port()
     mp.spawn(_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True)

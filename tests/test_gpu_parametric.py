@@ -10,7 +10,7 @@ import pytest
 from paper_1711_08013_gb300 import _binding as B
 from paper_1711_08013_gb300 import parametric as pm
 from paper_1711_08013_gb300 import problems as pb
-from tests.kkt_check import acceptance
+from tests.kkt_check import acceptance, objective, objective_interval
 
 pytestmark = pytest.mark.gpu
 
@@ -29,11 +29,24 @@ def replay(qp, trace):
 
 
 def check(oracle_mod, qs, steps, eps=1e-3):
+    """Each step's result against the oracle on the QP that step solved: the
+    acceptance test at ε, the oracle solving it too, and the GPU objective
+    inside the convexity interval around the oracle's optimum (ε = 1e-9);
+    at a tight ε (≤ 1e-6) also within 1e-4 (relative) of the oracle's
+    objective at the same ε."""
     for k, (q, st) in enumerate(zip(qs, steps)):
         assert st.status == B.SOLVED, (k, st.status)
         prim, dual, ep, ed = acceptance(q, st.x, st.y, eps, eps)
         assert prim <= 1.01 * ep and dual <= 1.01 * ed, (k, prim, ep, dual, ed)
-        assert oracle_mod.solve(q).status == oracle_mod.SOLVED
+        o = oracle_mod.solve(q, eps_abs=eps, eps_rel=eps, max_iter=200000)
+        assert o.status == oracle_mod.SOLVED
+        star = oracle_mod.solve(q, eps_abs=1e-9, eps_rel=1e-9, max_iter=800000)
+        lo, hi = objective_interval(q, st.x, st.z, st.y, star.x, star.y)
+        d = objective(q, st.x) - star.obj_val
+        slack = 1e-9 * max(1.0, abs(star.obj_val))
+        assert lo - slack <= d <= hi + slack, (k, lo, d, hi)
+        if eps <= 1e-6:
+            assert abs(objective(q, st.x) - o.obj_val) <= 1e-4 * max(1.0, abs(o.obj_val)), k
 
 
 @pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
@@ -76,3 +89,22 @@ def test_portfolio_backtest(oracle_mod):
     check(oracle_mod, qs, steps)
     for st in steps:
         assert abs(st.x[:n].sum() - 1.0) <= 1e-2 and st.x[:n].min() >= -1e-2
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
+def test_lasso_path_tight_eps(oracle_mod, precision):
+    """The warm-started λ-path at ε = 1e-6: every step's objective within
+    1e-4 of the oracle's on the same QP."""
+    qp = pb.lasso(10, seed=3)
+    trace = []
+    with pm.GpuSession(qp, precision=precision, eps_abs=1e-6, eps_rel=1e-6, max_iter=100000) as s:
+        ws = pm.run(s, pm.lasso_path(qp, 6), trace=trace)
+    check(oracle_mod, replay(qp, trace), ws, eps=1e-6)
+
+
+def test_mpc_closed_loop_tight_eps(oracle_mod):
+    qp = pb.mpc_paper(8, T=10, seed=4)
+    trace = []
+    with pm.GpuSession(qp, eps_abs=1e-6, eps_rel=1e-6, max_iter=100000) as s:
+        steps = pm.run(s, pm.mpc_closed_loop(qp, 6), trace=trace)
+    check(oracle_mod, replay(qp, trace), steps, eps=1e-6)

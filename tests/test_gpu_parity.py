@@ -237,3 +237,194 @@ def test_configs_full_size(oracle_mod, config, precision):
     d = objective(qp, g.x) - star.obj_val
     slack = 1e-6 * max(1.0, abs(star.obj_val))
     assert lo - slack <= d <= hi + slack, (lo, d, hi)
+
+
+# ---------------------------------------------------------------------------
+# ρ̄ adaptation (§5.2) step by step against the oracle
+# ---------------------------------------------------------------------------
+# classes whose ρ̄ moves within 60 iterations, with an iteration count a few
+# steps after the check of their first update (taken from the oracle)
+RHO_FIRST = {"random_qp": 28, "mpc": 23, "lasso": 53, "lasso_long": 43, "box": 28}
+RHO_CASES = [(name, qp, it) for name, qp in CLASSES if name in RHO_FIRST
+             for it in (RHO_FIRST[name], 60)]
+
+
+@pytest.mark.parametrize("launch", [1, 2, 3], ids=["block", "grid", "cluster"])
+@pytest.mark.parametrize("name,qp,iters", RHO_CASES,
+                         ids=[f"{c[0]}-{c[2]}" for c in RHO_CASES])
+def test_rho_adaptation_step_parity(oracle_mod, name, qp, iters, launch):
+    """With ρ̄ adaptation on (checks every 5 iterations, exact linear
+    solves), the GPU takes the same ρ̄ updates at the same checks as the
+    oracle (§5.2 rule in scaled norms, reading R6), ends at the same ρ̄, and
+    its iterates still equal the oracle's direct-method iterates across the
+    updates — the Jacobi rebuild on the device stands in for the oracle's
+    refactorisation."""
+    o = oracle_mod.solve(qp, max_iter=iters, **dict(STEP_ORACLE, adaptive_rho=1, check_interval=5))
+    with Solver(qp, max_iter=iters, launch=launch,
+                **dict(STEP_GPU, adaptive_rho=1, check_interval=5, pcg_max_iter=20000)) as s:
+        g = s.solve()
+    assert o.rho_updates >= 1, name  # the case exercises at least one update
+    assert g.iter == iters
+    assert g.rho_updates == o.rho_updates, (name, g.rho_updates, o.rho_updates)
+    # ρ̄ is a square root of a ratio of residual norms, and a residual near
+    # convergence is a small difference of large terms: iterates equal to
+    # ~1e-10 give ratios equal to ~1e-8 relative (lasso: 1.6e-8), far inside
+    # the factor-5 rule that decides an update
+    assert abs(g.rho_estimate - o.rho_bar) <= 1e-6 * o.rho_bar, (name, g.rho_estimate, o.rho_bar)
+    assert rel_err(g.x, o.x) <= 1e-8, name
+    assert rel_err(g.z, o.z) <= 1e-8, name
+    assert rel_err(g.y, o.y) <= 1e-8, name
+
+
+# ---------------------------------------------------------------------------
+# Scaling and the Jacobi diagonal read back from the device
+# ---------------------------------------------------------------------------
+def host_jacobi(qp, scaled, rho_bar, sigma):
+    """diag(P̄) + σ + Σ_i ρ_i Ā_ij² from the oracle's scaled data, with
+    ρ_i = ρ̄, or 10³ρ̄ on rows with l_i == u_i (§5.2)."""
+    Pf = qp.P_full()
+    Pb = sp.csc_matrix((scaled["P_x"], Pf.indices, Pf.indptr), shape=Pf.shape)
+    Ab = sp.csc_matrix((scaled["A_x"], qp.A.indices, qp.A.indptr), shape=qp.A.shape)
+    rho = np.where(qp.l == qp.u, 1e3 * rho_bar, rho_bar)
+    return Pb.diagonal() + sigma + np.asarray(Ab.multiply(Ab).T @ rho).ravel()
+
+
+JAC_CLASSES = CLASSES + [("portfolio_full", pb.config_problem(2))]
+
+
+@pytest.mark.parametrize("launch", [1, 2], ids=["block", "grid"])
+@pytest.mark.parametrize("name,qp", JAC_CLASSES, ids=[c[0] for c in JAC_CLASSES])
+def test_scaling_and_jacobi_diagonal(oracle_mod, name, qp, launch):
+    """D, E, c of Alg. 2 and the Jacobi diagonal of P̄ + σI + ĀᵀRĀ on the
+    device equal the values built on the host from the oracle's Ruiz
+    scaling, after setup and after ρ̄ changes (osqp_update_rho, and the
+    adaptive updates of a solve)."""
+    sigma = 1e-6
+    scaled = oracle_mod.ruiz(qp.P_full(), qp.q, qp.A, qp.l, qp.u)
+    with Solver(qp, launch=launch, sigma=sigma) as s:
+        D, E, c, dg = s.scaling()
+        assert rel_err(D, scaled["D"]) <= 1e-12 and rel_err(E, scaled["E"]) <= 1e-12
+        assert abs(c - scaled["c"]) <= 1e-12 * scaled["c"]
+        want = host_jacobi(qp, scaled, 0.1, sigma)
+        assert np.max(np.abs(dg - want) / want) <= 1e-12, name
+        s.update_rho(3.7)
+        dg = s.scaling()[3]
+        want = host_jacobi(qp, scaled, 3.7, sigma)
+        assert np.max(np.abs(dg - want) / want) <= 1e-12, name
+        g = s.solve()
+        dg = s.scaling()[3]
+        want = host_jacobi(qp, scaled, g.rho_estimate, sigma)
+        assert np.max(np.abs(dg - want) / want) <= 1e-12, (name, g.rho_updates)
+
+
+# ---------------------------------------------------------------------------
+# High-accuracy runs at full size (ε = 1e-5, §3.4)
+# ---------------------------------------------------------------------------
+_STAR = {}
+
+
+def oracle_at(oracle_mod, key, qp, eps):
+    k = (key, eps)
+    if k not in _STAR:
+        _STAR[k] = oracle_mod.solve(qp, eps_abs=eps, eps_rel=eps, max_iter=800000, check_interval=25)
+    return _STAR[k]
+
+
+HI_FULL = {0: lambda: pb.config_problem(0), 1: lambda: pb.config_problem(1),
+           2: lambda: pb.config_problem(2)}
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("config", list(HI_FULL))
+def test_high_accuracy_full_size(oracle_mod, config, precision):
+    """The single-problem configurations at full size, ε = 1e-5, in the
+    launch shape the benchmark uses: the acceptance test at 1e-5 on the
+    host, the objective inside the convexity interval around the oracle's
+    optimum (ε = 1e-9), and the objective within 1e-4 (relative) of the
+    oracle's ε = 1e-5 objective.  On the portfolio problem two ε = 1e-5
+    points can differ by more than that (the oracle's own ε = 1e-5 and 1e-9
+    objectives differ by 1.6e-3, reading R20), so the 1e-4 bound is taken
+    there at ε = 1e-7, where the oracle itself is within 5e-6 of its optimum."""
+    qp = HI_FULL[config]()
+    star = oracle_at(oracle_mod, config, qp, 1e-9)
+    o5 = oracle_at(oracle_mod, config, qp, 1e-5)
+    assert star.status == oracle_mod.SOLVED and o5.status == oracle_mod.SOLVED
+    with Solver(qp, precision=precision, eps_abs=1e-5, eps_rel=1e-5, max_iter=200000) as s:
+        g = s.solve()
+    assert g.status == B.SOLVED, (config, g.status, g.iter)
+    prim, dual, ep, ed = acceptance(qp, g.x, g.y, 1e-5, 1e-5)
+    assert prim <= ep * 1.01 and dual <= ed * 1.01, (prim, ep, dual, ed)
+    lo, hi = objective_interval(qp, g.x, g.z, g.y, star.x, star.y)
+    f = objective(qp, g.x)
+    d = f - star.obj_val
+    slack = 1e-9 * max(1.0, abs(star.obj_val))
+    assert lo - slack <= d <= hi + slack, (lo, d, hi)
+    scale = max(1.0, abs(o5.obj_val))
+    if config != 2:
+        assert abs(f - o5.obj_val) <= 1e-4 * scale, (f, o5.obj_val)
+    else:
+        o7 = oracle_at(oracle_mod, config, qp, 1e-7)
+        with Solver(qp, precision=precision, eps_abs=1e-7, eps_rel=1e-7, max_iter=400000) as s:
+            g7 = s.solve()
+        assert g7.status == B.SOLVED, (g7.status, g7.iter)
+        f7 = objective(qp, g7.x)
+        assert abs(f7 - o7.obj_val) <= 1e-4 * max(1.0, abs(o7.obj_val)), (f7, o7.obj_val)
+
+
+def mpc_sample(count=4096, every=16, seed=3000):
+    """Every 16th problem of the 4096-problem batched MPC workload, generated
+    alone with the batch's own draws."""
+    rng = np.random.default_rng(seed)
+    nxs = rng.integers(4, 33, size=count)
+    Ts = rng.integers(10, 31, size=count)
+    return [pb.mpc(int(nxs[i]), int(Ts[i]), seed=seed + 1 + i) for i in range(0, count, every)]
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
+def test_high_accuracy_batch_sample(oracle_mod, precision):
+    """256 problems of the batched MPC workload in one batch launch at
+    ε = 1e-5: every result passes the acceptance test at 1e-5 and lies in
+    the convexity interval around the oracle's optimum; at ε = 1e-6 every
+    objective is within 1e-4 (relative) of the oracle's (at ε = 1e-5 two
+    ε-points of these problems can differ by more: the oracle's own 1e-5
+    objectives are up to 1e-4 from its optimum)."""
+    from paper_1711_08013_gb300.solver import BatchSolver
+    qps = mpc_sample()
+    stars = [oracle_mod.solve(q, eps_abs=1e-9, eps_rel=1e-9, max_iter=800000) for q in qps]
+    o6 = [oracle_mod.solve(q, eps_abs=1e-6, eps_rel=1e-6, max_iter=200000) for q in qps]
+    for eps in (1e-5, 1e-6):
+        with BatchSolver(qps, precision=precision, eps_abs=eps, eps_rel=eps, max_iter=200000) as bs:
+            bs.solve()
+            res = [bs.result(i) for i in range(len(qps))]
+        worst = 0.0
+        for k, (q, r, st) in enumerate(zip(qps, res, stars)):
+            assert r.status == B.SOLVED, (k, r.status, r.iter)
+            prim, dual, ep, ed = acceptance(q, r.x, r.y, eps, eps)
+            assert prim <= ep * 1.01 and dual <= ed * 1.01, (k, prim, ep, dual, ed)
+            lo, hi = objective_interval(q, r.x, r.z, r.y, st.x, st.y)
+            d = objective(q, r.x) - st.obj_val
+            slack = 1e-9 * max(1.0, abs(st.obj_val))
+            assert lo - slack <= d <= hi + slack, (k, lo, d, hi)
+            if eps == 1e-6:
+                e = abs(objective(q, r.x) - o6[k].obj_val) / max(1.0, abs(o6[k].obj_val))
+                worst = max(worst, e)
+        if eps == 1e-6:
+            assert worst <= 1e-4, worst
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("launch", [1, 2, 3], ids=["block", "grid", "cluster"])
+def test_long_rows_are_deterministic(launch, precision):
+    """The portfolio problem at full size (a 10 000-entry budget row and 100
+    rows of 5 000 entries in Ā: long rows summed chunk by chunk): two solves
+    from the same start take the same PCG iterations and return bit-identical
+    iterates, whichever warps finish the long rows."""
+    qp = pb.config_problem(2)
+    out = []
+    for _ in range(2):
+        with Solver(qp, launch=launch, precision=precision, max_iter=200) as s:
+            g = s.solve()
+        out.append(g)
+    a, b = out
+    assert a.pcg_iters == b.pcg_iters and a.iter == b.iter
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.y, b.y) and np.array_equal(a.z, b.z)

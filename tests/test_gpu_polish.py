@@ -28,18 +28,26 @@ CASES = [
 ]
 
 
+_BLOCK64 = {}
+
+
 @pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("launch", [1, 2, 3], ids=["block", "grid", "cluster"])
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
 def test_polish_reaches_high_accuracy(oracle_mod, name, make, launch, precision):
+    """Every case polishes on the one-CTA FP64 solver, and every other team
+    shape and precision polishes it too (its ADMM point differs at the
+    rounding level, not in the active set that the signs of y give)."""
     qp = make()
     hi = oracle_mod.solve(qp, **HIGH)
+    if name not in _BLOCK64:
+        with Solver(qp, launch=1, precision=B.FP64, polish=1) as s:
+            _BLOCK64[name] = s.solve().polished
     with Solver(qp, launch=launch, precision=precision, polish=1) as s:
         g = s.solve()
     assert g.status == B.SOLVED
-    assert g.polished in (1, -1)
-    if launch == 1 and precision == B.FP64:
-        assert g.polished == 1, name
+    assert _BLOCK64[name] == 1, name
+    assert g.polished == 1, (name, g.polished)
     if g.polished == 1:
         prim, dual, ep, ed = acceptance(qp, g.x, g.y, 1e-8, 1e-8)
         assert prim <= ep and dual <= ed, (name, prim, ep, dual, ed)

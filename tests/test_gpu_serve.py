@@ -7,7 +7,7 @@ import pytest
 
 from paper_1711_08013_gb300 import _binding as B
 from paper_1711_08013_gb300 import problems as pb
-from tests.kkt_check import acceptance
+from tests.kkt_check import acceptance, objective, objective_interval
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +62,13 @@ def test_serving_overlap_matches_alone_and_oracle(oracle_mod):
             assert prim <= 1.01 * ep and dual <= 1.01 * ed, (pid, prim, ep, dual, ed)
             o = oracle_mod.solve(qp2)
             assert o.status == oracle_mod.SOLVED
+            # the served objective against the oracle's optimum of the same
+            # perturbed QP: inside the convexity interval
+            star = oracle_mod.solve(qp2, eps_abs=1e-9, eps_rel=1e-9, max_iter=800000)
+            lo, hi = objective_interval(qp2, x, z, y, star.x, star.y)
+            d = objective(qp2, x) - star.obj_val
+            slack = 1e-9 * max(1.0, abs(star.obj_val))
+            assert lo - slack <= d <= hi + slack, (pid, lo, d, hi)
 
 
 def test_deadline_drops_unlaunched_requests():
@@ -106,3 +113,22 @@ def test_large_requests_on_clusters():
     qp2 = pb._finish("req", qps[big].P, last.q, qps[big].A, last.l, last.u)
     prim, dual, ep, ed = acceptance(qp2, last.x, y, 1e-3, 1e-3)
     assert prim <= 1.01 * ep and dual <= 1.01 * ed
+
+
+def test_served_results_match_oracle_at_tight_eps(oracle_mod):
+    """Served at ε = 1e-6 with overlapping slots: every request's objective
+    is within 1e-4 (relative) of the oracle's solution of the same perturbed
+    QP at the same ε, and passes the acceptance test at 1e-6."""
+    qps = pool()
+    reqs = poisson_requests(qps, rate=2000.0, duration=0.02, seed=17)
+    assert len(reqs) >= 20
+    with Server(qps, slots=4, eps_abs=1e-6, eps_rel=1e-6, max_iter=100000) as srv:
+        mix = clone(reqs)
+        srv.run(mix, keep_x=True)
+    for r in mix:
+        assert r.status == B.SOLVED, (r.pid, r.status)
+        qp2 = pb._finish("req", qps[r.pid].P, r.q, qps[r.pid].A, r.l, r.u)
+        o = oracle_mod.solve(qp2, eps_abs=1e-6, eps_rel=1e-6, max_iter=200000)
+        assert o.status == oracle_mod.SOLVED
+        f = objective(qp2, r.x)
+        assert abs(f - o.obj_val) <= 1e-4 * max(1.0, abs(o.obj_val)), (r.pid, f, o.obj_val)

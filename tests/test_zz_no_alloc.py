@@ -161,3 +161,87 @@ def test_noalloc_captured_in_cuda_graph_replays_a_control_loop():
         assert rc == B.OSQP_OK and ref.status == B.SOLVED
         assert info.status == ref.status and info.iter == ref.iter, (step, info.iter, ref.iter)
         assert _rel(xg, xr) <= 1e-12 and _rel(yg, yr) <= 1e-12, step
+
+
+def _raw_call(torch, f, n, m, Pp, Pi, Px, q, Ap, Ai, Ax, l, u, st):
+    """One call on device copies of raw CSC arrays (buffer sizes always match
+    the stated n, m and nonzero counts, so a rejected input is only ever
+    malformed in its contents)."""
+    dev = torch.device("cuda", 0)
+    ti = lambda a: torch.tensor(np.asarray(a, dtype=np.int32), device=dev)
+    tf = lambda a: torch.tensor(np.asarray(a, dtype=np.float64), device=dev)
+    d = [ti(Pp), ti(Pi), tf(Px), tf(q), ti(Ap), ti(Ai), tf(Ax), tf(l), tf(u)]
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    y = torch.zeros(max(m, 1), dtype=torch.float64, device=dev)
+    info = B.osqp_info()
+    rc = f(n, m, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), len(Px), d[3].data_ptr(),
+           d[4].data_ptr(), d[5].data_ptr(), d[6].data_ptr(), len(Ax), d[7].data_ptr(),
+           d[8].data_ptr(), C.byref(st), x.data_ptr(), y.data_ptr(), C.byref(info), None)
+    torch.cuda.synchronize()
+    return rc
+
+
+def _bad_inputs():
+    eye4 = dict(Pp=[0, 1, 2, 3, 4], Pi=[0, 1, 2, 3], Px=[1.0, 1.0, 1.0, 1.0])
+    a4 = dict(Ap=[0, 1, 2, 3, 4], Ai=[0, 0, 1, 1], Ax=[1.0, 1.0, 1.0, 1.0])
+    base = dict(n=4, m=2, q=[1.0, -1.0, 0.5, 0.0], l=[-1.0, -1.0], u=[1.0, 1.0], **eye4, **a4)
+    cases = []
+    cases.append(("colptr_decreasing", dict(base, Pp=[0, 2, 1, 3, 4]), B.OSQP_ERR_CSC))
+    cases.append(("lower_triangle_in_P", dict(base, Pp=[0, 2, 3, 4, 4], Pi=[0, 1, 1, 2]),
+                  B.OSQP_ERR_CSC))
+    cases.append(("unsorted_A_column", dict(base, Ap=[0, 2, 2, 3, 4], Ai=[1, 0, 1, 1]),
+                  B.OSQP_ERR_CSC))
+    cases.append(("nan_in_q", dict(base, q=[1.0, float("nan"), 0.0, 0.0]), B.OSQP_ERR_NONFINITE))
+    cases.append(("inf_in_A", dict(base, Ax=[1.0, float("inf"), 1.0, 1.0]), B.OSQP_ERR_NONFINITE))
+    cases.append(("nan_bound", dict(base, u=[1.0, float("nan")]), B.OSQP_ERR_NONFINITE))
+    cases.append(("l_above_u", dict(base, l=[-1.0, 2.0]), B.OSQP_ERR_LGTU))
+    # one A row of 8193 entries (above the 8192-entry row limit)
+    n = 8193
+    cases.append(("long_A_row", dict(n=n, m=1, Pp=list(range(n + 1)), Pi=list(range(n)),
+                                     Px=[1.0] * n, q=[0.0] * n, Ap=list(range(n + 1)),
+                                     Ai=[0] * n, Ax=[1.0] * n, l=[-1.0], u=[1.0]),
+                  B.OSQP_ERR_LIMIT))
+    # a P row of 8193 entries in the full symmetric matrix (row 0 dense)
+    Pp, Pi = [0, 1], [0]
+    for j in range(1, n):
+        Pi += [0, j]
+        Pp.append(len(Pi))
+    cases.append(("long_P_row", dict(n=n, m=0, Pp=Pp, Pi=Pi, Px=[1e-3] * len(Pi), q=[0.0] * n,
+                                     Ap=[0] * (n + 1), Ai=[], Ax=[], l=[], u=[]),
+                  B.OSQP_ERR_LIMIT))
+    return cases
+
+
+BAD = _bad_inputs()
+
+
+@pytest.mark.gpu
+def test_noalloc_rejects_bad_inputs_on_the_device_then_recovers():
+    """The input checks of osqp_setup run inside the kernel here: malformed
+    CSC, non-finite values, l > u and rows beyond the 8192-entry limit each
+    give their error code from the call and again from
+    osqp_noalloc_get_info, and a valid solve in the same array afterwards
+    still equals the allocating entry point's."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    f, gi = noalloc_fn(), get_info_fn()
+    st = B.osqp_set_default_settings(launch=1)
+    for name, c, want in BAD:
+        rc = _raw_call(torch, f, c["n"], c["m"], c["Pp"], c["Pi"], c["Px"], c["q"], c["Ap"],
+                       c["Ai"], c["Ax"], c["l"], c["u"], st)
+        assert rc == want, (name, rc)
+        info = B.osqp_info()
+        rc2 = gi(c["n"], c["m"], len(c["Px"]), len(c["Ax"]), B.FP64, C.byref(info), None)
+        assert rc2 == want, (name, rc2)
+    from paper_1711_08013_gb300.solver import Solver
+    qp = pb.random_qp(30, 90, seed=31)
+    with Solver(qp, launch=1) as s:
+        ref = s.solve()
+    d = _device_inputs(torch, qp)
+    x = torch.empty(qp.n, dtype=torch.float64, device="cuda")
+    y = torch.empty(qp.m, dtype=torch.float64, device="cuda")
+    rc, info, xg, yg = _call(torch, f, qp, d, st, x, y)
+    assert rc == B.OSQP_OK and info.status == ref.status and info.iter == ref.iter
+    assert _rel(xg, ref.x) <= 1e-8 and _rel(yg, ref.y) <= 1e-8
