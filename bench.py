@@ -64,8 +64,8 @@ PARAM_LEN = {"lasso_path": 100, "mpc_loop": 100, "portfolio_bt": 960}
 # kernels as they are now; for the batch, the capture of the first 608
 # problems scaled by the problems of the launch.  Absent: not captured
 # since the kernels last changed.
-TRAFFIC = {}
-TRAFFIC_BATCH_PER_PROBLEM = {}
+TRAFFIC = {("lasso", "fp64"): 19.661056e6}
+TRAFFIC_BATCH_PER_PROBLEM = {"fp32": 3.536293e9 / 608}
 # Mean time per QP and mean iterations per QP that the paper reports for the
 # same sequences (OSQP direct method on a CPU; context only)
 PARAM_PAPER = {

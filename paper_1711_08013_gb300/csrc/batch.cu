@@ -30,10 +30,9 @@ constexpr long long kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchCluster = 8;      // CTAs of a heavy-problem cluster
 constexpr int kMaxHeavyClusters = 4;  // clusters a launch may take for heavy problems
 constexpr int kMaxHeavy = 32;         // heavy problems per launch at most
-constexpr size_t kPrefetchBytes = 512 << 10;  // matrix bytes above which a batch problem
-                                              // prefetches its slices into L2
 constexpr long long kClusterWork = 1 << 17;  // nonzeros of Kn + Ā from which a slot launch
                                              // solves its problems on clusters
+constexpr size_t kPoolCap = 160 << 10;  // shared memory for one problem's PCG vectors at most
 
 enum : int { kModeScale = 1, kModeRefresh = 2, kModeReset = 4 };
 
@@ -73,12 +72,48 @@ __device__ void batch_solve_one(Team& tm, const Dev<T>& d, const Params& P, int 
   admm_stage(tm, d, P);
 }
 
+// As batch_solve_one, with the PCG vectors in the CTA's shared memory (one
+// CTA per problem; the problem's vectors fit in `pool`).
+template <typename T>
+__device__ void batch_solve_one_smem(BlockTeam& tm, const Dev<T>& d, const Params& P, int md,
+                                     Dev<T>& sd, unsigned char* pool) {
+  const double rho_bar = d.sc->rho_bar;
+  if (md & kModeScale) {
+    if (!scale_stage(tm, d, P, rho_bar, true)) return;
+  } else {
+    if ((md & kModeRefresh) && !refresh_stage(tm, d, P, rho_bar)) return;
+    if (md & kModeReset) {
+      if (tm.leader()) {
+        d.sc->rp_last = 0.0;
+        d.sc->rd_last = 0.0;
+      }
+      for (int j = tm.tid(); j < d.n; j += tm.nthreads()) {
+        d.x[j] = 0.0;
+        d.dx[j] = 0.0;
+        d.xt[j] = 0.0;
+      }
+      for (int i = tm.tid(); i < d.m; i += tm.nthreads()) {
+        d.z[i] = 0.0;
+        d.y[i] = 0.0;
+        d.dy[i] = 0.0;
+        d.zt[i] = 0.0;
+      }
+    }
+  }
+  stage_in(d, sd, pool);
+  admm_stage(tm, sd, P);
+  stage_out(d, sd);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBatchThreads, 1)
     k_batch(const Dev<T>* __restrict__ devs, const int* __restrict__ order, int count,
-            const __grid_constant__ Params P, int* queue, unsigned long long* times) {
+            const __grid_constant__ Params P, int* queue, unsigned long long* times,
+            int pool_bytes) {
   __shared__ double sm[kSmemDoubles];
   __shared__ int sidx;
+  __shared__ Dev<T> sdev;
+  extern __shared__ __align__(16) unsigned char pool[];
   BlockTeam tm{sm};
   for (;;) {
     if (threadIdx.x == 0) sidx = atomicAdd(queue, 1);
@@ -90,7 +125,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     const int p = code & ((1 << kModeShift) - 1);
     const Dev<T>& d = devs[p];
     const unsigned long long t0 = gtimer();
-    batch_solve_one(tm, d, P, code >> kModeShift);
+    if (smem_vec_bytes<T>(d.n, d.m) <= (size_t)pool_bytes)
+      batch_solve_one_smem(tm, d, P, code >> kModeShift, sdev, pool);
+    else
+      batch_solve_one(tm, d, P, code >> kModeShift);
     __syncthreads();
     if (threadIdx.x == 0) {
       times[2 * p] = t0;
@@ -224,11 +262,12 @@ size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
   const size_t a_cc = b.take<unsigned>(L.a_s.lrange.size());
   const size_t rt = b.take<uint8_t>(m);
   const size_t pact = b.take<uint8_t>(m);
-  size_t on[22], om[22], otn[11], otm[6];
+  size_t on[22], om[22], otn[10], otm[4], out[2];
   for (auto& v : on) v = b.take<double>(n);
   for (auto& v : om) v = b.take<double>(m);
   for (auto& v : otn) v = b.take<T>(n);
   for (auto& v : otm) v = b.take<T>(m);
+  for (auto& v : out) v = b.take<T>(n + m);
   const size_t sc = b.take<Scalars>(1);
   if (base && d) {
     d->kn_v = (T*)(base + kn_v);
@@ -248,11 +287,12 @@ size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
                      &d->dy, &d->ax, &d->adx, &d->azt, &d->z_out, &d->y_out, &d->pcert,
                      &d->zt, &d->wm, &d->um, &d->Einv, &d->pol_y, &d->pol_t, &d->pol_r2};
     for (int k = 0; k < 22; ++k) *mv[k] = (double*)(base + om[k]);
-    T** tn[] = {&d->dinv, &d->b, &d->mr, &d->p, &d->r0, &d->r1, &d->s0, &d->s1, &d->w0, &d->w1,
-                &d->dxt};
-    for (int k = 0; k < 11; ++k) *tn[k] = (T*)(base + otn[k]);
-    T** tmv[] = {&d->rt0, &d->rt1, &d->ap, &d->dzt, &d->rhoT, &d->rho_invT};
-    for (int k = 0; k < 6; ++k) *tmv[k] = (T*)(base + otm[k]);
+    T** tn[] = {&d->dinv, &d->b, &d->p, &d->r0, &d->r1, &d->s0, &d->s1, &d->w0, &d->w1, &d->dxt};
+    for (int k = 0; k < 10; ++k) *tn[k] = (T*)(base + otn[k]);
+    T** tmv[] = {&d->ap, &d->dzt, &d->rhoT, &d->rho_invT};
+    for (int k = 0; k < 4; ++k) *tmv[k] = (T*)(base + otm[k]);
+    d->ut0 = (T*)(base + out[0]);
+    d->ut1 = (T*)(base + out[1]);
     d->sc = (Scalars*)(base + sc);
   }
   return (b.off + 255) & ~(size_t)255;
@@ -262,6 +302,7 @@ size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
 
 struct osqp_batch {
   int count = 0, device = 0, num_sms = 0, grid = 0;
+  int pool = 0;  // dynamic shared memory of k_batch: PCG vectors of problems that fit
   cudaStream_t stream = nullptr;
   osqp_settings set{};
   Params P{};
@@ -342,15 +383,10 @@ void fill_batch_devs(osqp_batch* b) {
                    (const int2*)(sb + so.rng),
                    (const int*)(sb + so.li),
                    nullptr,   // cpart, ccount: carved in the dynamic block below
-                   nullptr,
-                   0};  // prefetch: set below from the matrix bytes
+                   nullptr};
     };
     d->kn = sched(L.kn_s, o.kn, L.n);
     d->as = sched(L.a_s, o.a, L.m);
-    // a problem whose matrices exceed its share of L2 among the concurrent
-    // problems streams them from DRAM: prefetch its slices
-    const size_t mat_bytes = (size_t)(L.kn_s.npos + L.a_s.npos) * (sizeof(int) + sizeof(T));
-    d->kn.prefetch = d->as.prefetch = mat_bytes > kPrefetchBytes ? 1 : 0;
     dynamic_carve<T>(L, b->arena + L.v_off, d);
   }
 }
@@ -479,8 +515,8 @@ int launch_batch(osqp_batch* b, const std::vector<int>& sel, int* order_d, int* 
   if (nl) {
     // leave the clusters' SMs to them whichever kernel the GPU starts first
     const int grid = std::max(1, std::min(b->grid - nclusters * kBatchCluster, nl));
-    k_batch<T><<<grid, kBatchThreads, 0, st>>>((const Dev<T>*)b->devs, order_d, nl, b->P, queue,
-                                                b->times_d);
+    k_batch<T><<<grid, kBatchThreads, b->pool, st>>>((const Dev<T>*)b->devs, order_d, nl, b->P,
+                                                      queue, b->times_d, b->pool);
     if (cudaGetLastError() != cudaSuccess) return OSQP_ERR_CUDA;
   }
   if (nh && cudaStreamWaitEvent(st, b->cjoin, 0) != cudaSuccess) return OSQP_ERR_CUDA;
@@ -599,12 +635,36 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
   if (cudaGetDevice(&b->device) != cudaSuccess) return fail(OSQP_ERR_CUDA);
   if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
     return fail(OSQP_ERR_CUDA);
+  // Shared memory for the PCG vectors of one problem: the largest need of
+  // the batch, capped (problems above the cap keep their vectors in HBM).
+  {
+    size_t need = 0;
+    for (int i = 0; i < count; ++i) {
+      const size_t v = settings->precision == OSQP_PRECISION_FP64
+                           ? smem_vec_bytes<double>(P[i].n_cols, A[i].n_rows)
+                           : smem_vec_bytes<float>(P[i].n_cols, A[i].n_rows);
+      if (v <= kPoolCap) need = std::max(need, v);
+    }
+    b->pool = (int)need;
+    // the attribute is the cap for every batch (a per-batch value would race
+    // with other batches' launches)
+    const cudaError_t ea =
+        settings->precision == OSQP_PRECISION_FP64
+            ? cudaFuncSetAttribute(k_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kPoolCap)
+            : cudaFuncSetAttribute(k_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kPoolCap);
+    if (ea != cudaSuccess) {
+      cudaGetLastError();
+      b->pool = 0;
+    }
+  }
   int occ = 0;
   cudaError_t e = settings->precision == OSQP_PRECISION_FP64
                       ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<double>,
-                                                                      kBatchThreads, 0)
+                                                                      kBatchThreads, b->pool)
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<float>,
-                                                                      kBatchThreads, 0);
+                                                                      kBatchThreads, b->pool);
   if (e != cudaSuccess) return fail(OSQP_ERR_CUDA);
   b->grid = b->num_sms * std::max(1, occ);
 

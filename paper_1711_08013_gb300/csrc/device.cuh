@@ -71,7 +71,6 @@ struct Sched {
   double* cpart;        // per chunk: kMaxNV partial values of the current product
   unsigned* ccount;     // per long row: chunks stored in the current product
                         // (zero between products: the completing warp resets it)
-  int prefetch;         // 1: stream the slices into L2 ahead of use (data not L2-resident)
 };
 
 struct Barrier {
@@ -117,10 +116,12 @@ struct Dev {
   T* dinv;
   double *x, *z, *y, *dx, *dy;
   double *xt, *zt, *wm, *um;  // x̃, z̃ and the RHS inputs stay FP64 in both modes
-  // PCG vectors (working precision): b, mr = M⁻¹r, p; r, s = Kp, w = K·mr
-  // and t = R·Ā·mr double-buffered; ap = Āp (for z̃ = Āx̃)
-  T *b, *mr, *p, *r0, *r1, *s0, *s1, *w0, *w1;
-  T *rt0, *rt1, *ap;
+  // PCG vectors (working precision): b, p; r, s = Kp and w = Ku
+  // double-buffered; u = M⁻¹r and t = RĀu double-buffered as one array
+  // [u | t] of n + m values each (ut0, ut1), so that a product with
+  // Kn = [P̄ Āᵀ] gathers both from one base; ap = Āp (for z̃ = Āx̃)
+  T *b, *p, *r0, *r1, *s0, *s1, *w0, *w1;
+  T *ut0, *ut1, *ap;
   // PCG corrections of x̃ and z̃ in working precision, folded into the FP64
   // x̃, z̃ once per ADMM iteration; working-precision copies of ρ and ρ⁻¹
   T *dxt, *dzt, *rhoT, *rho_invT;
@@ -566,18 +567,6 @@ struct PlainTeam {
 // combines them by a fixed shuffle tree, so a row's result does not depend on
 // where its slice sits, and a long row's result not on which warp finished it.
 // ---------------------------------------------------------------------------
-// Bulk prefetch of one slice's column indices and values into L2 (a slice
-// occupies 32·steps consecutive positions starting at a multiple of 32, so
-// both ranges are 16-byte aligned multiples of 16 bytes).
-template <typename MT>
-__device__ __forceinline__ void prefetch_slice(int2 sl, const int* ci, const MT* va) {
-  if (sl.y <= 0) return;
-  const unsigned bi = 32u * sl.y * (unsigned)sizeof(int);
-  const unsigned bv = 32u * sl.y * (unsigned)sizeof(MT);
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ci + sl.x), "r"(bi) : "memory");
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(va + sl.x), "r"(bv) : "memory");
-}
-
 // Arrival of one chunk at its row's counter: a release add (the chunk's
 // partial, stored just before by the same thread, is published with it).
 // The warp that completes the count then takes an acquire fence before it
@@ -702,15 +691,7 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* 
   const int spw = 32 / Gw;
   const int gw = lane / Gw;
   const unsigned gmask = (Gw == 32) ? 0xffffffffu : (((1u << Gw) - 1u) << (gw * Gw));
-  // Problems whose data do not stay in L2 (set by the batch for its largest
-  // problems) ask for each warp's slices two steps ahead, so the index/value
-  // stream arrives from DRAM while the dependent gathers run.
-  if (S.prefetch && lane == 0)
-    for (int s = tm.warp(); s < S.nslices && s < tm.warp() + 2 * nwt; s += nwt)
-      prefetch_slice(S.slices[s], ci, va);
   for (int s = tm.warp(); s < S.nslices; s += nwt) {
-    if (S.prefetch && lane == 0 && s + 2 * nwt < S.nslices)
-      prefetch_slice(S.slices[s + 2 * nwt], ci, va);
     const int2 sl = S.slices[s];
     const int row = S.srow[s * spw + gw];
     AT acc[NV];
@@ -1224,6 +1205,60 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
 }
 
 // ---------------------------------------------------------------------------
+// Working-precision vectors of a one-CTA solve in shared memory.  The PCG
+// vectors (p, r, s, w, the x̃ correction, the Jacobi inverse; [u | t]; Āp,
+// the z̃ correction, ρ and ρ⁻¹ in working precision) are read and written
+// every PCG iteration and gathered by both sparse products; for a problem
+// whose vectors fit, admm_stage runs on a copy of the problem's Dev whose
+// pointers to them address the CTA's shared memory.  Only the Jacobi
+// inverse and the ρ vectors carry values into and out of a solve.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+template <typename T>
+__host__ __device__ constexpr size_t smem_vec_bytes(int n, int m) {
+  return 9 * align16((size_t)n * sizeof(T)) + 2 * align16((size_t)(n + m) * sizeof(T)) +
+         4 * align16((size_t)m * sizeof(T));
+}
+
+template <typename T>
+__device__ void stage_in(const Dev<T>& d, Dev<T>& sd, unsigned char* pool) {
+  if (threadIdx.x == 0) {
+    sd = d;
+    size_t off = 0;
+    auto take = [&](int count) {
+      T* q = reinterpret_cast<T*>(pool + off);
+      off += align16((size_t)count * sizeof(T));
+      return q;
+    };
+    T** nv[] = {&sd.p, &sd.r0, &sd.r1, &sd.s0, &sd.s1, &sd.w0, &sd.w1, &sd.dxt, &sd.dinv};
+    for (T** q : nv) *q = take(d.n);
+    sd.ut0 = take(d.n + d.m);
+    sd.ut1 = take(d.n + d.m);
+    T** mv[] = {&sd.ap, &sd.dzt, &sd.rhoT, &sd.rho_invT};
+    for (T** q : mv) *q = take(d.m);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < d.n; j += blockDim.x) sd.dinv[j] = d.dinv[j];
+  for (int i = threadIdx.x; i < d.m; i += blockDim.x) {
+    sd.rhoT[i] = d.rhoT[i];
+    sd.rho_invT[i] = d.rho_invT[i];
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void stage_out(const Dev<T>& d, const Dev<T>& sd) {
+  __syncthreads();
+  for (int j = threadIdx.x; j < d.n; j += blockDim.x) d.dinv[j] = sd.dinv[j];
+  for (int i = threadIdx.x; i < d.m; i += blockDim.x) {
+    d.rhoT[i] = sd.rhoT[i];
+    d.rho_invT[i] = sd.rho_invT[i];
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Stage 2: Algorithm 1 with the indirect linear solve of §3.1.
 // ---------------------------------------------------------------------------
 template <class Team, typename T>
@@ -1256,14 +1291,13 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   double* __restrict__ wm = d.wm;
   double* __restrict__ um = d.um;
   T* __restrict__ bv = d.b;
-  T* __restrict__ u = d.mr;  // u = M⁻¹r
   T* __restrict__ pv = d.p;
   T* __restrict__ ap = d.ap;
   // double-buffer selection without a local-memory pointer table
   auto rbuf = [&](int i) { return i ? d.r1 : d.r0; };
   auto sbuf = [&](int i) { return i ? d.s1 : d.s0; };
   auto wbuf = [&](int i) { return i ? d.w1 : d.w0; };
-  auto tbuf = [&](int i) { return i ? d.rt1 : d.rt0; };
+  auto ubuf = [&](int i) { return i ? d.ut1 : d.ut0; };  // [u | t]
   T* __restrict__ dinv = d.dinv;
   T* __restrict__ dxt = d.dxt;
   T* __restrict__ dzt = d.dzt;
@@ -1356,7 +1390,8 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     T red3t[3];
     {
       const T* __restrict__ r = rbuf(cur);
-      T* __restrict__ t = tbuf(cur);
+      T* __restrict__ u = ubuf(cur);
+      T* __restrict__ t = ubuf(cur) + n;
       T a0 = T(0), a1 = T(0), a2 = T(0);
       for (int j = tid; j < n; j += nth) {
         const T rj = r[j];
@@ -1394,11 +1429,11 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       double red1[1] = {0.0};
       T wacc = T(0);
       T* __restrict__ w = wbuf(cur);
-      const T* __restrict__ tg = tbuf(cur);
+      const T* __restrict__ ut = ubuf(cur);
+      const T* __restrict__ u = ut;
       // long rows of w stay as chunk partials: P1, the only reader, sums them
       spmv<1, false, T, T>(
-          tm, d.kn, kn_ci, kn_v,
-          [&](int col, T v, T* acc) { acc[0] += v * (col < n ? u[col] : tg[col - n]); },
+          tm, d.kn, kn_ci, kn_v, [&](int col, T v, T* acc) { acc[0] += v * ut[col]; },
           [&](int j, T* acc) {
             const T wj = sigT * u[j] + acc[0];
             w[j] = wj;
@@ -1435,7 +1470,9 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         const T* __restrict__ wc = wbuf(cur);
         T* __restrict__ rn = rbuf(nxt);
         T* __restrict__ sn = sbuf(nxt);
-        const T* __restrict__ tc = tbuf(cur);
+        const T* __restrict__ tc = ubuf(cur) + n;
+        const T* __restrict__ u = ubuf(cur);
+        T* __restrict__ un = ubuf(nxt);
         const bool lazy_w = d.kn.nlong > 0;
         for (int j = tid; j < n; j += nth) {
           T wj;  // w = Ku, its long rows summed here from the product's partials
@@ -1448,7 +1485,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           dxt[j] += aT * pj;
           const T rj = rc[j] - aT * sj;
           rn[j] = rj;
-          u[j] = rj * dinv[j];
+          un[j] = rj * dinv[j];
         }
         for (int i = tid; i < m; i += nth) {
           const T ti = rho_invT[i] * tc[i];
@@ -1460,7 +1497,8 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       if (!tm.sync()) return false;
       // --- P1b: t' = RĀu
       {
-        T* __restrict__ tn = tbuf(nxt);
+        const T* __restrict__ u = ubuf(nxt);
+        T* __restrict__ tn = ubuf(nxt) + n;
         spmv<1, false, T, T>(
             tm, d.as, a_ci, a_v, [&](int col, T v, T* acc) { acc[0] += v * u[col]; },
             [&](int i, T* acc) { tn[i] = rhoT[i] * acc[0]; });
@@ -1474,16 +1512,16 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       {
         const T* __restrict__ rn = rbuf(nxt);
         T* __restrict__ wn = wbuf(nxt);
+        const T* __restrict__ ut = ubuf(nxt);
+        const T* __restrict__ u = ut;
         T g0 = T(0), g1 = T(0), g2 = T(0);
         for (int j = tid; j < n; j += nth) {
           const T rj = rn[j];
           g0 += rj * u[j];
           g2 = fmax(g2, fabs(rj));
         }
-        const T* __restrict__ tg = tbuf(nxt);
         spmv<1, false, T, T>(
-            tm, d.kn, kn_ci, kn_v,
-            [&](int col, T v, T* acc) { acc[0] += v * (col < n ? u[col] : tg[col - n]); },
+            tm, d.kn, kn_ci, kn_v, [&](int col, T v, T* acc) { acc[0] += v * ut[col]; },
             [&](int j, T* acc) {
               const T wj = sigT * u[j] + acc[0];
               wn[j] = wj;

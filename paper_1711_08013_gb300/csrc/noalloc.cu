@@ -160,14 +160,16 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
   const int first_m = c;
   for (int k = 0; k < nvec_m; ++k) o[c++] = L.template take<double>(m);
   const int first_tn = c;
-  for (int k = 0; k < 11; ++k) o[c++] = L.template take<T>(n);
+  for (int k = 0; k < 10; ++k) o[c++] = L.template take<T>(n);
   const int at_rt = c;
-  for (int k = 0; k < 6; ++k) o[c++] = L.template take<T>(m);
+  for (int k = 0; k < 4; ++k) o[c++] = L.template take<T>(m);
+  const int at_ut = c;
+  for (int k = 0; k < 2; ++k) o[c++] = L.template take<T>(n + m);
   const int at_sc = c;
   o[c++] = L.template take<Scalars>(1);
   const int at_err = c;
   o[c++] = L.template take<int>(2);
-  static_assert(38 + 22 + 22 + 11 + 6 + 2 <= kSlots, "scratch slot table too small");
+  static_assert(38 + 22 + 22 + 10 + 4 + 2 + 2 <= kSlots, "scratch slot table too small");
   if (base && p) {
     Dev<T>& d = p->d;
     d.n = in.n;
@@ -203,10 +205,12 @@ __host__ __device__ size_t na_carve(const NaInput& in, char* base, NaPtrs<T>* p)
                      &d.ax, &d.adx, &d.azt, &d.z_out, &d.y_out, &d.pcert, &d.zt, &d.wm, &d.um,
                      &d.Einv, &d.pol_y, &d.pol_t, &d.pol_r2};
     for (int k = 0; k < nvec_m; ++k) *mv[k] = (double*)(base + o[first_m + k]);
-    T** tv[] = {&d.dinv, &d.b, &d.mr, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1, &d.dxt};
-    for (int k = 0; k < 11; ++k) *tv[k] = (T*)(base + o[first_tn + k]);
-    T** tmv[] = {&d.rt0, &d.rt1, &d.ap, &d.dzt, &d.rhoT, &d.rho_invT};
-    for (int k = 0; k < 6; ++k) *tmv[k] = (T*)(base + o[at_rt + k]);
+    T** tv[] = {&d.dinv, &d.b, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1, &d.dxt};
+    for (int k = 0; k < 10; ++k) *tv[k] = (T*)(base + o[first_tn + k]);
+    T** tmv[] = {&d.ap, &d.dzt, &d.rhoT, &d.rho_invT};
+    for (int k = 0; k < 4; ++k) *tmv[k] = (T*)(base + o[at_rt + k]);
+    d.ut0 = (T*)(base + o[at_ut]);
+    d.ut1 = (T*)(base + o[at_ut + 1]);
     d.sc = (Scalars*)(base + o[at_sc]);
     p->err = (int*)(base + o[at_err]);
     p->flag = p->err + 1;
@@ -407,7 +411,6 @@ __device__ bool build_sliced(Sched& S, const NaSched& B, NaPtrs<T>& sp, int nrow
       S.lidx = B.lidx;
       S.cpart = B.cpart;
       S.ccount = B.ccount;
-      S.prefetch = 0;
     }
   }
   __syncthreads();

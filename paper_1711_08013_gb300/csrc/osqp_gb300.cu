@@ -99,12 +99,23 @@ OSQP_CLUSTER_KERNEL(k_scale_cluster, scale_stage(tm, d, P, rho_bar, reset != 0),
 OSQP_CLUSTER_KERNEL(k_refresh_cluster, refresh_stage(tm, d, P, rho_bar), double rho_bar)
 #undef OSQP_CLUSTER_KERNEL
 
+// One-CTA solve; with pool_bytes > 0 the PCG vectors live in the CTA's
+// shared memory (pool_bytes ≥ smem_vec_bytes of the problem).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_admm_block(const __grid_constant__ Dev<T> d,
-                                                          const __grid_constant__ Params P) {
+                                                          const __grid_constant__ Params P,
+                                                          int pool_bytes) {
   __shared__ double sm[kSmemDoubles];
+  __shared__ Dev<T> sdev;
+  extern __shared__ __align__(16) unsigned char pool[];
   BlockTeam tm{sm};
-  admm_stage(tm, d, P);
+  if (pool_bytes > 0) {
+    stage_in(d, sdev, pool);
+    admm_stage(tm, sdev, P);
+    stage_out(d, sdev);
+  } else {
+    admm_stage(tm, d, P);
+  }
 }
 
 // raw value gather: dst[k] = src[idx[k]], 0 where idx[k] < 0 (layout padding)
@@ -188,9 +199,11 @@ __global__ void k_zero_iterates(const __grid_constant__ Dev<T> d) {
 // ---------------------------------------------------------------------------
 
 constexpr int kClusterSize = 8;  // CTAs of a cluster team (portable maximum)
+constexpr size_t kBlockPoolCap = 160 << 10;  // shared memory for a one-CTA solve's PCG vectors
 
 struct osqp_solver {
   int device = 0, num_sms = 0, grid = 0, use_grid = 0, use_cluster = 0;
+  int pool = 0;  // dynamic shared memory of the one-CTA solve (0: vectors in HBM)
   cudaStream_t stream = nullptr;
   osqp_settings set{};
   Params P{};
@@ -245,7 +258,6 @@ void take_sched(Arena& A, const SchedHost& h, int nrows, Sched& S) {
   S.lidx = A.take<int>(h.lidx.size());
   S.cpart = A.take<double>(h.chunks.size() * kMaxNV);
   S.ccount = A.take<unsigned>(h.lrange.size());
-  S.prefetch = 0;  // one problem's data stay in L2
 }
 
 template <typename T>
@@ -275,9 +287,11 @@ void fill_dev(osqp_solver* s, Arena& A, Dev<T>& d) {
                      &d.zt, &d.wm, &d.um, &d.Einv, &d.pol_y, &d.pol_t, &d.pol_r2};
   for (double** p : mvec) *p = A.take<double>(m);
   d.pol_act = A.take<uint8_t>(m);
-  T** tn[] = {&d.dinv, &d.b, &d.mr, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1};
+  T** tn[] = {&d.dinv, &d.b, &d.p, &d.r0, &d.r1, &d.s0, &d.s1, &d.w0, &d.w1};
   for (T** p : tn) *p = A.take<T>(n);
-  T** tmv[] = {&d.rt0, &d.rt1, &d.ap, &d.dzt, &d.rhoT, &d.rho_invT};
+  d.ut0 = A.take<T>((size_t)n + m);
+  d.ut1 = A.take<T>((size_t)n + m);
+  T** tmv[] = {&d.ap, &d.dzt, &d.rhoT, &d.rho_invT};
   for (T** p : tmv) *p = A.take<T>(m);
   d.dxt = A.take<T>(n);
 }
@@ -370,7 +384,7 @@ int launch_admm(osqp_solver* s) {
     CK(cudaLaunchCooperativeKernel((const void*)k_admm_grid<T>, dim3(s->grid), dim3(kThreads), args,
                                    0, s->stream));
   } else {
-    k_admm_block<T><<<1, kThreads, 0, s->stream>>>(d, s->P);
+    k_admm_block<T><<<1, kThreads, s->pool, s->stream>>>(d, s->P, s->pool);
     CK(cudaGetLastError());
   }
   return OSQP_OK;
@@ -701,6 +715,22 @@ int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const 
     while (per_sm > 1 && s->num_sms * per_sm > 512) --per_sm;
   }
   s->grid = s->num_sms * per_sm;
+  if (!s->use_grid && !s->use_cluster) {
+    const size_t need = settings->precision == OSQP_PRECISION_FP64 ? smem_vec_bytes<double>(n, m)
+                                                                   : smem_vec_bytes<float>(n, m);
+    if (need <= kBlockPoolCap) {
+      // the attribute is the cap for every solver (a per-solver value would
+      // race with other solvers' launches)
+      const cudaError_t ea =
+          settings->precision == OSQP_PRECISION_FP64
+              ? cudaFuncSetAttribute(k_admm_block<double>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlockPoolCap)
+              : cudaFuncSetAttribute(k_admm_block<float>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlockPoolCap);
+      if (ea == cudaSuccess) s->pool = (int)need;
+      else cudaGetLastError();
+    }
+  }
   {
     const long long nwarps =
         (long long)(s->use_grid ? s->grid : (s->use_cluster ? kClusterSize : 1)) * (kThreads / 32);
