@@ -90,6 +90,10 @@ def parse():
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
     ap.add_argument("--nmax", type=int, default=500, help="serve: largest problem dimension n")
+    ap.add_argument("--large-slots", type=int, default=16,
+                    help="serve: launch slots that large (cluster) requests may hold at once")
+    ap.add_argument("--rates", type=lambda v: [float(x) for x in v.split(",")], default=None,
+                    help="serve: comma-separated offered rates to sweep before the headline run")
     ap.add_argument("--seq-len", type=int, default=None,
                     help="parametric workloads: QPs of the sequence (default: the paper's length)")
     args = ap.parse_args()
@@ -594,48 +598,99 @@ def batch_error(qps, results, idx, out):
             "dual_res_over_eps_max": max(e["dual_res"] / e["eps_dual"] for e in errs)}
 
 
+def serve_spec(nmax, seed=4000, pool=256):
+    return pb.serving_pool_spec(seed=seed, pool=pool, n_range=(10, nmax))
+
+
+def serve_problem(entry):
+    cls, n, sd = entry
+    return pb.random_qp(n, seed=sd) if cls == "random_qp" else pb.huber(n, seed=sd)
+
+
 def serve_pool(nmax, seed=4000):
-    spec = pb.serving_pool_spec(seed=seed, pool=256, n_range=(10, nmax))
-    return [pb.random_qp(n, seed=sd) if cls == "random_qp" else pb.huber(n, seed=sd)
-            for cls, n, sd in spec]
+    return [serve_problem(e) for e in serve_spec(nmax, seed)]
+
+
+def serve_work(entry):
+    """Estimated matrix entries of a pool problem (random QP: m = 10n rows at
+    15%; Huber: 100n × n data at 15% plus the identity blocks)."""
+    cls, n, _ = entry
+    return 1.5 * n * n if cls == "random_qp" else 15.0 * n * n + 400.0 * n
 
 
 def serve_main(args, ws, rank, local):
     """Serving workload: the request stream is the step; value = achieved
     solves/s, with offered load, p50/p99 latency (arrival → result on the host)
-    and queueing reported beside it."""
+    and queueing reported beside it.  One global pool of problem IDs is
+    sharded across ranks by LPT on estimated work; each rank serves the
+    requests of the global stream that name its IDs.  --rates adds a sweep of
+    offered rates (each run for --duration seconds) and the highest of them
+    at which fewer than 1% of the requests were dropped."""
     import torch
     from paper_1711_08013_gb300 import _binding as B
     from paper_1711_08013_gb300 import dist as D
-    from paper_1711_08013_gb300.serve import Server, poisson_requests
+    from paper_1711_08013_gb300.serve import Server, poisson_requests, shard_requests
     torch.cuda.set_device(local)
     if ws > 1:
         D.init("nccl", torch.device("cuda", local))
-    qps = serve_pool(args.nmax, seed=4000 + 7919 * rank)
+    dev = torch.device("cuda", local)
+    spec = serve_spec(args.nmax, seed=4000)
+    mine = D.shard([serve_work(e) for e in spec], rank, ws)
+    local_of = {g: k for k, g in enumerate(mine)}
+    qps = [serve_problem(spec[g]) for g in mine]
     prec = B.FP64 if args.precision == "fp64" else B.FP32_MIXED
-    srv = Server(qps, slots=32, precision=prec)
-    warm = poisson_requests(qps, args.rate, min(2.0, args.duration), seed=1 + rank)
-    srv.run(warm, max_batch=8, deadline=min(2.0, args.duration))
-    reqs = poisson_requests(qps, args.rate, args.duration, seed=100 + rank)
+    slots, large_slots = 32, args.large_slots
+    srv = Server(qps, slots=slots, precision=prec, large_slots=large_slots)
+
+    def stream(rate, duration, seed):
+        """The global request stream (identical on every rank: the generator
+        draws every request's perturbation from one stream, on the sizes of
+        other ranks' IDs too), kept for this rank's IDs."""
+        shapes = [qps[local_of[g]] if g in local_of else _shape_qp(spec[g])
+                  for g in range(len(spec))]
+        return shard_requests(poisson_requests(shapes, rate, duration, seed=seed), mine)
+
+    def one(rate, duration, seed):
+        reqs = stream(rate, duration, seed)
+        st = srv.run(reqs, deadline=duration)
+        served = [r for r in reqs if r.t_done == r.t_done]
+        offered = D.sum_over_ranks(float(len(reqs)), device=dev)
+        done = D.sum_over_ranks(float(st.requests), device=dev)
+        dropped = D.sum_over_ranks(float(st.dropped), device=dev)
+        wall = D.max_over_ranks(st.wall, device=dev)
+        return st, reqs, served, offered, done, dropped, wall
+
+    one(args.rate, min(2.0, args.duration), 1)  # warm-up stream
+    sweep = []
+    for rate in (args.rates or []):
+        st, reqs, served, offered, done, dropped, wall = one(rate, args.duration, 200 + int(rate))
+        sweep.append({"offered_req_per_s": rate, "offered": int(offered), "served": int(done),
+                      "dropped": int(dropped), "achieved_req_per_s": done / wall,
+                      "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+                      "drop_frac": dropped / max(1.0, offered)})
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    st = srv.run(reqs, max_batch=8, deadline=args.duration)
+    st, reqs, served, offered, total, dropped, wall = one(args.rate, args.duration, 100)
     clocks = sampler.stop()
-    served = [r for r in reqs if r.t_done == r.t_done]
     bad = sum(r.status != B.SOLVED for r in served)
-    wall = D.max_over_ranks(st.wall, device="cuda")
-    total = D.sum_over_ranks(float(st.requests), device="cuda")
+    ok_rates = [w["offered_req_per_s"] for w in sweep if w["drop_frac"] < 0.01]
     line = {
         "metric": METRIC, "value": total / wall, "unit": UNIT, "n_gpus": ws, "steps": 1,
         "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == B.FP64 else "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOADS["serve"][1].replace("NMAX", str(args.nmax)),
                    "offered_req_per_s": args.rate, "duration_s": args.duration,
-                   "pool": len(qps), "slots": 32, "max_batch": 8, "precision": args.precision,
-                   "eps": 1e-3},
+                   "pool": len(spec), "slots": slots, "large_slots": large_slots,
+                   "max_batch": None, "precision": args.precision, "eps": 1e-3,
+                   "parallelism": (f"pool of {len(spec)} IDs sharded over {ws} GPUs (LPT on "
+                                   "estimated work)") if ws > 1 else "single"},
         "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_queue_ms": st.mean_queue_ms,
-        "launches": st.launches, "not_solved": bad, "offered": len(reqs), "dropped": st.dropped,
+        "launches": st.launches, "not_solved": bad, "offered": int(offered),
+        "dropped": int(dropped),
+        "host_launch_s": st.host_launch_s, "host_result_s": st.host_result_s,
         "mean_iters": float(np.mean([r.iter for r in served])) if served else 0.0,
+        "sweep": sweep,
+        "max_rate_under_1pct_drop": max(ok_rates) if ok_rates else None,
         "e2e": {"value": total / wall, "unit": UNIT,
                 "h2d_bytes_per_step": int(8 * sum(qps[r.pid].n + 2 * qps[r.pid].m for r in served)),
                 "d2h_bytes_per_step": int(8 * sum(qps[r.pid].n + 2 * qps[r.pid].m for r in served))},
@@ -648,6 +703,16 @@ def serve_main(args, ws, rank, local):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _shape_qp(entry):
+    """Sizes of a pool problem without its matrices: q, l, u of the right
+    lengths (the request generator perturbs those)."""
+    cls, n, sd = entry
+    import types
+    m = 10 * n if cls == "random_qp" else 3 * 100 * n
+    nn = n if cls == "random_qp" else n + 3 * 100 * n
+    return types.SimpleNamespace(n=nn, m=m, q=np.zeros(nn), l=-np.ones(m), u=np.ones(m))
 
 
 def param_main(args, ws, rank, local):

@@ -112,6 +112,11 @@ typedef struct {
                                     residuals are no larger.  Default 0 */
   int32_t polish_refine_iter;    /* refinement passes, default 3 */
   double delta;                  /* δ of Eq. (kkt_polish_reg), default 1e-6 */
+  int32_t autotune;              /* batch only: 1 = time the candidate row partitions
+                                    (group widths 1…32) of each shape class of
+                                    matrices at osqp_batch_setup and use the fastest;
+                                    0 = the row-length rule.  Default 1 */
+  int32_t pad2;
 } osqp_settings;
 
 typedef struct {
@@ -282,6 +287,19 @@ int32_t osqp_batch_uses_cluster(const osqp_batch* b, int32_t i);
 
 /* Device bytes that problem i occupies (its data, iterates and work arrays). */
 int64_t osqp_batch_footprint(const osqp_batch* b, int32_t i);
+
+/* Row partition of problem i (a schedule choice; the paper has no
+ * counterpart): groups[0] and groups[1] receive the lanes per row (group
+ * width G of the sliced layout) of its Kn = [P̄ Āᵀ] and Ā products. */
+int32_t osqp_batch_schedule(const osqp_batch* b, int32_t i, int32_t* groups);
+
+/* The autotuner's table (settings->autotune): one entry per shape class of
+ * matrices.  Returns the number of classes (0 when the rule was used); for
+ * k < min(classes, cap), info[6k .. 6k+5] = {kind (0 Kn, 1 Ā), log2-rows
+ * bucket, mean-length bucket, log2-longest-row bucket, representative
+ * problem, chosen G} and cycles[6k .. 6k+5] = the measured cycles of G = 1, 2,
+ * 4, 8, 16, 32 (host arrays, may be NULL).  OSQP_ERR_ARG for a NULL batch. */
+int32_t osqp_batch_tuning(const osqp_batch* b, int32_t cap, int32_t* info, double* cycles);
 
 int32_t osqp_batch_cleanup(osqp_batch* b);
 

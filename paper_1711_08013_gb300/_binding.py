@@ -42,7 +42,7 @@ class osqp_settings(C.Structure):
         ("scaling_iters", C.c_int32), ("max_rho_updates", C.c_int32),
         ("pcg_max_iter", C.c_int32), ("precision", C.c_int32), ("warm_start", C.c_int32),
         ("launch", C.c_int32), ("polish", C.c_int32), ("polish_refine_iter", C.c_int32),
-        ("delta", C.c_double),
+        ("delta", C.c_double), ("autotune", C.c_int32), ("pad2", C.c_int32),
     ]
 
 
@@ -93,6 +93,8 @@ _SIGS = {
     "osqp_batch_slot_query": (C.c_int32, [_P, C.c_int32]),
     "osqp_batch_slot_wait": (C.c_int32, [_P, C.c_int32]),
     "osqp_batch_footprint": (C.c_int64, [_P, C.c_int32]),
+    "osqp_batch_schedule": (C.c_int32, [_P, C.c_int32, _P]),
+    "osqp_batch_tuning": (C.c_int32, [_P, C.c_int32, _P, _P]),
 }
 OSQP_BATCH_MAX_SLOTS = 32
 
@@ -348,3 +350,22 @@ def osqp_batch_footprint(h, i) -> int:
     if v < 0:
         _check(int(v), "osqp_batch_footprint")
     return int(v)
+
+
+def osqp_batch_schedule(h, i):
+    g = np.zeros(2, np.int32)
+    _check(lib().osqp_batch_schedule(h, int(i), _ptr(g)), "osqp_batch_schedule")
+    return int(g[0]), int(g[1])
+
+
+def osqp_batch_tuning(h):
+    """The autotuner's classes: list of (kind, rows bucket, mean bucket,
+    longest-row bucket, representative, chosen G, cycles of G = 1…32)."""
+    n = lib().osqp_batch_tuning(h, 0, None, None)
+    if n < 0:
+        _check(n, "osqp_batch_tuning")
+    info = np.zeros(6 * max(n, 1), np.int32)
+    cyc = np.zeros(6 * max(n, 1))
+    lib().osqp_batch_tuning(h, n, _ptr(info), _ptr(cyc))
+    return [tuple(int(v) for v in info[6 * k:6 * k + 6]) + (cyc[6 * k:6 * k + 6].copy(),)
+            for k in range(n)]

@@ -11,7 +11,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -191,6 +194,51 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   cluster_sync_all();
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the row partition.  For every class of matrices of similar
+// shape (rows, mean and longest row, in powers of two), one representative
+// matrix is laid out with each candidate group width G and one CTA per
+// (class, candidate) times `reps` products y = M x on the batch kernel's team
+// shape, with x in shared memory as in the batched solve; the fastest G of
+// each class is used for every matrix of the class.
+// ---------------------------------------------------------------------------
+constexpr int kTuneGroups[] = {1, 2, 4, 8, 16, 32};
+constexpr int kTuneCandidates = 6;
+constexpr int kTuneReps = 40;
+
+template <typename T>
+struct TuneCase {
+  Sched S;
+  const int* ci;
+  const T* va;
+  T* xg;   // x in global memory when it does not fit the shared pool
+  T* y;
+  int ncols, pad;
+  unsigned long long* cycles;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads, 1)
+    k_tune(const TuneCase<T>* __restrict__ cases, int reps, int pool_bytes) {
+  __shared__ double sm[kSmemDoubles];
+  extern __shared__ __align__(16) unsigned char pool[];
+  const TuneCase<T>& c = cases[blockIdx.x];
+  T* x = (size_t)c.ncols * sizeof(T) <= (size_t)pool_bytes ? reinterpret_cast<T*>(pool) : c.xg;
+  for (int j = threadIdx.x; j < c.ncols; j += blockDim.x) x[j] = T(1) + T(j & 7) * T(0.125);
+  __syncthreads();
+  BlockTeam tm{sm};
+  T* __restrict__ y = c.y;
+  auto store = [&](int row, T* acc) { y[row] = acc[0]; };
+  const long long t0 = clock64();
+  for (int r = 0; r < reps; ++r) {
+    spmv<1, false, T, T>(tm, c.S, c.ci, c.va, [&](int col, T v, T* acc) { acc[0] += v * x[col]; },
+                         store, NoChunk{}, store);
+    __syncthreads();
+  }
+  const long long t1 = clock64();
+  if (threadIdx.x == 0) *c.cycles = (unsigned long long)(t1 - t0);
+}
+
 // Per-problem sizes and offsets.
 struct ProblemLayout {
   int n = 0, m = 0, nnz_kn = 0, nnz_a = 0;
@@ -303,6 +351,14 @@ size_t dynamic_carve(const ProblemLayout& L, char* base, Dev<T>* d) {
 struct osqp_batch {
   int count = 0, device = 0, num_sms = 0, grid = 0;
   int pool = 0;  // dynamic shared memory of k_batch: PCG vectors of problems that fit
+  // autotuner: per class (matrix kind 0 = Kn, 1 = Ā; shape key; representative
+  // problem), the cycles of each candidate group width and the choice
+  struct TuneClass {
+    int kind, rows_b, mean_b, max_b, rep, chosen;
+    double cycles[kTuneCandidates];
+  };
+  std::vector<TuneClass> tune;
+  std::vector<int2> groups;  // per problem: group width of Kn and of Ā
   cudaStream_t stream = nullptr;
   osqp_settings set{};
   Params P{};
@@ -529,6 +585,184 @@ int launch_batch(osqp_batch* b, const std::vector<int>& sel, int* order_d, int* 
   return OSQP_OK;
 }
 
+// Shape class of a matrix given by its CSR row pointers.
+std::array<int, 3> tune_key(const std::vector<int>& rp) {
+  const int nrows = (int)rp.size() - 1;
+  int maxlen = 0;
+  for (int r = 0; r < nrows; ++r) maxlen = std::max(maxlen, rp[r + 1] - rp[r]);
+  const double mean = nrows > 0 ? (double)rp[nrows] / nrows : 0.0;
+  auto lg = [](double v) { return (int)std::floor(std::log2(v + 1.0)); };
+  return {lg(nrows), (int)std::floor(2.0 * std::log2(mean + 1.0)), lg(maxlen)};
+}
+
+// Measure every candidate group width on one representative matrix per
+// shape class (one launch of k_tune, one CTA per case) and set each
+// problem's widths to its classes' fastest.  Returns OSQP_OK or a CUDA error
+// code; on any failure the rule's widths stay in force.
+template <typename T>
+int autotune_groups(osqp_batch* b, const std::vector<HostStructure>& hs) {
+  const int count = b->count;
+  std::map<std::array<int, 4>, int> cls;  // (kind, key) → class index
+  std::vector<int> cls_of(2 * (size_t)count);
+  b->tune.clear();
+  for (int i = 0; i < count; ++i)
+    for (int kind = 0; kind < 2; ++kind) {
+      const auto k = tune_key(kind == 0 ? hs[i].kn_rp : hs[i].a_rp);
+      const std::array<int, 4> key{kind, k[0], k[1], k[2]};
+      auto it = cls.find(key);
+      if (it == cls.end()) {
+        osqp_batch::TuneClass tc{};
+        tc.kind = kind;
+        tc.rows_b = k[0];
+        tc.mean_b = k[1];
+        tc.max_b = k[2];
+        tc.rep = i;
+        tc.chosen = 0;
+        it = cls.emplace(key, (int)b->tune.size()).first;
+        b->tune.push_back(tc);
+      }
+      cls_of[2 * (size_t)i + kind] = it->second;
+    }
+  // candidate layouts of each representative, packed into one device buffer
+  struct Cand {
+    SchedHost S;
+    std::vector<int> ci;
+    int nrows, ncols;
+  };
+  std::vector<Cand> cands;
+  for (const auto& tc : b->tune) {
+    const HostStructure& h = hs[tc.rep];
+    const std::vector<int>& rp = tc.kind == 0 ? h.kn_rp : h.a_rp;
+    const std::vector<int>& ci = tc.kind == 0 ? h.kn_ci : h.a_ci;
+    for (int g : kTuneGroups) {
+      Cand c;
+      c.S = make_sched(rp, kBatchWarps, g);
+      c.ci = to_positions(c.S, ci, -1);
+      c.S.pos = {};
+      c.nrows = (int)rp.size() - 1;
+      c.ncols = tc.kind == 0 ? h.n + h.m : h.n;
+      cands.push_back(std::move(c));
+    }
+  }
+  Bump bump;
+  struct Off {
+    size_t ci, va, sl, sr, ch, lr, rng, li, cp, cc, xg, y, cyc;
+  };
+  std::vector<Off> off(cands.size());
+  int max_cols = 0;
+  for (size_t k = 0; k < cands.size(); ++k) {
+    const Cand& c = cands[k];
+    Off& o = off[k];
+    o.ci = bump.take<int>(c.S.npos);
+    o.va = bump.take<T>(c.S.npos);
+    o.sl = bump.take<int2>(c.S.slices.size());
+    o.sr = bump.take<int>(c.S.srow.size());
+    o.ch = bump.take<int4>(c.S.chunks.size());
+    o.lr = bump.take<int>(c.S.long_rows.size());
+    o.rng = bump.take<int2>(c.S.lrange.size());
+    o.li = bump.take<int>(c.S.lidx.size());
+    o.cp = bump.take<double>(c.S.chunks.size() * kMaxNV);
+    o.cc = bump.take<unsigned>(c.S.lrange.size());
+    o.xg = bump.take<T>(c.ncols);
+    o.y = bump.take<T>(c.nrows);
+    o.cyc = bump.take<unsigned long long>(1);
+    max_cols = std::max(max_cols, c.ncols);
+  }
+  const size_t cases_off = bump.take<TuneCase<T>>(cands.size());
+  const size_t total = bump.off;
+  std::vector<char> hbuf(total, 0);
+  char* dbuf = nullptr;
+  if (cudaMalloc((void**)&dbuf, total) != cudaSuccess) {
+    cudaGetLastError();
+    return OSQP_ERR_OOM;
+  }
+  std::vector<TuneCase<T>> tcs(cands.size());
+  for (size_t k = 0; k < cands.size(); ++k) {
+    const Cand& c = cands[k];
+    const Off& o = off[k];
+    auto put = [&](size_t at, const void* src, size_t bytes) {
+      if (bytes) std::memcpy(hbuf.data() + at, src, bytes);
+    };
+    put(o.ci, c.ci.data(), sizeof(int) * c.ci.size());
+    T* va = reinterpret_cast<T*>(hbuf.data() + o.va);
+    for (int q = 0; q < c.S.npos; ++q) va[q] = c.ci[q] >= 0 ? T(1) : T(0);
+    put(o.sl, c.S.slices.data(), sizeof(int2) * c.S.slices.size());
+    put(o.sr, c.S.srow.data(), sizeof(int) * c.S.srow.size());
+    put(o.ch, c.S.chunks.data(), sizeof(int4) * c.S.chunks.size());
+    put(o.lr, c.S.long_rows.data(), sizeof(int) * c.S.long_rows.size());
+    put(o.rng, c.S.lrange.data(), sizeof(int2) * c.S.lrange.size());
+    put(o.li, c.S.lidx.data(), sizeof(int) * c.S.lidx.size());
+    TuneCase<T>& t = tcs[k];
+    t.S = Sched{c.nrows,
+                c.S.group,
+                c.S.long_thresh,
+                (int)c.S.chunks.size(),
+                (int)c.S.long_rows.size(),
+                (int)c.S.slices.size(),
+                (const int2*)(dbuf + o.sl),
+                (const int*)(dbuf + o.sr),
+                (const int4*)(dbuf + o.ch),
+                (const int*)(dbuf + o.lr),
+                (const int2*)(dbuf + o.rng),
+                (const int*)(dbuf + o.li),
+                (double*)(dbuf + o.cp),
+                (unsigned*)(dbuf + o.cc)};
+    t.ci = (const int*)(dbuf + o.ci);
+    t.va = (const T*)(dbuf + o.va);
+    t.xg = (T*)(dbuf + o.xg);
+    t.y = (T*)(dbuf + o.y);
+    t.ncols = c.ncols;
+    t.pad = 0;
+    t.cycles = (unsigned long long*)(dbuf + o.cyc);
+  }
+  std::memcpy(hbuf.data() + cases_off, tcs.data(), sizeof(TuneCase<T>) * tcs.size());
+  const int xpool = (int)std::min<size_t>(kPoolCap, (size_t)max_cols * sizeof(T));
+  int rc = OSQP_OK;
+  if (cudaMemcpy(dbuf, hbuf.data(), total, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tune<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kPoolCap) != cudaSuccess)
+    rc = OSQP_ERR_CUDA;
+  std::vector<unsigned long long> best(cands.size(), ~0ull);
+  // two timed launches after a warm one; the faster of the two per case
+  for (int pass = 0; rc == OSQP_OK && pass < 3; ++pass) {
+    k_tune<T><<<(int)cands.size(), kBatchThreads, xpool, b->stream>>>(
+        (const TuneCase<T>*)(dbuf + cases_off), kTuneReps, xpool);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+      rc = OSQP_ERR_CUDA;
+      break;
+    }
+    if (pass == 0) continue;
+    for (size_t k = 0; k < cands.size(); ++k) {
+      unsigned long long cy = 0;
+      if (cudaMemcpy(&cy, dbuf + off[k].cyc, sizeof(cy), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = OSQP_ERR_CUDA;
+        break;
+      }
+      best[k] = std::min(best[k], cy);
+    }
+  }
+  cudaFree(dbuf);
+  if (rc != OSQP_OK) {
+    cudaGetLastError();
+    b->tune.clear();
+    return rc;
+  }
+  for (size_t c = 0; c < b->tune.size(); ++c) {
+    osqp_batch::TuneClass& tc = b->tune[c];
+    int bi = 0;
+    for (int g = 0; g < kTuneCandidates; ++g) {
+      tc.cycles[g] = (double)best[c * kTuneCandidates + g];
+      if (best[c * kTuneCandidates + g] < best[c * kTuneCandidates + bi]) bi = g;
+    }
+    tc.chosen = kTuneGroups[bi];
+  }
+  b->groups.assign(count, make_int2(0, 0));
+  for (int i = 0; i < count; ++i)
+    b->groups[i] = make_int2(b->tune[cls_of[2 * (size_t)i]].chosen,
+                             b->tune[cls_of[2 * (size_t)i + 1]].chosen);
+  return OSQP_OK;
+}
+
 int batch_launch(osqp_batch* b, const std::vector<int>& sel) {
   if (cudaEventRecord(b->ev[0], b->stream) != cudaSuccess) return OSQP_ERR_CUDA;
   const int rc = b->set.precision == OSQP_PRECISION_FP64
@@ -673,15 +907,23 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
   std::vector<HostStructure> hs(count);
   b->L.resize(count);
   size_t s_total = 0;
+  for (int i = 0; i < count; ++i) build_host_structure(&P[i], &A[i], &hs[i]);
+  // row partition: measured per shape class (settings->autotune), else the rule
+  b->groups.assign(count, make_int2(0, 0));
+  if (settings->autotune) {
+    const int rt = settings->precision == OSQP_PRECISION_FP64 ? autotune_groups<double>(b, hs)
+                                                             : autotune_groups<float>(b, hs);
+    if (rt == OSQP_ERR_CUDA) return fail(rt);
+    if (rt != OSQP_OK) b->groups.assign(count, make_int2(0, 0));
+  }
   for (int i = 0; i < count; ++i) {
-    build_host_structure(&P[i], &A[i], &hs[i]);
     ProblemLayout& L = b->L[i];
     L.n = hs[i].n;
     L.m = hs[i].m;
     L.nnz_kn = hs[i].nnz_kn;
     L.nnz_a = hs[i].nnz_a;
-    L.kn_s = make_sched(hs[i].kn_rp, kBatchWarps);
-    L.a_s = make_sched(hs[i].a_rp, kBatchWarps);
+    L.kn_s = make_sched(hs[i].kn_rp, kBatchWarps, b->groups[i].x);
+    L.a_s = make_sched(hs[i].a_rp, kBatchWarps, b->groups[i].y);
     L.s_off = s_total;
     s_total += static_offsets(L).end;
   }
@@ -1003,6 +1245,27 @@ int32_t osqp_batch_slot_wait(osqp_batch* b, int32_t slot) {
 int32_t osqp_batch_uses_cluster(const osqp_batch* b, int32_t i) {
   if (!b || i < 0 || i >= b->count) return OSQP_ERR_ARG;
   return (b->cluster_ok && b->set.launch != 1 && large_problem(b, i)) ? 1 : 0;
+}
+
+int32_t osqp_batch_schedule(const osqp_batch* b, int32_t i, int32_t* groups) {
+  if (!b || !groups || i < 0 || i >= b->count) return OSQP_ERR_ARG;
+  groups[0] = b->L[i].kn_s.group;
+  groups[1] = b->L[i].a_s.group;
+  return OSQP_OK;
+}
+
+int32_t osqp_batch_tuning(const osqp_batch* b, int32_t cap, int32_t* info, double* cycles) {
+  if (!b) return OSQP_ERR_ARG;
+  const int nc = (int)b->tune.size();
+  for (int k = 0; k < nc && k < cap; ++k) {
+    const osqp_batch::TuneClass& t = b->tune[k];
+    if (info) {
+      const int32_t v[6] = {t.kind, t.rows_b, t.mean_b, t.max_b, t.rep, t.chosen};
+      std::memcpy(info + 6 * k, v, sizeof(v));
+    }
+    if (cycles) std::memcpy(cycles + 6 * k, t.cycles, sizeof(t.cycles));
+  }
+  return nc;
 }
 
 int64_t osqp_batch_footprint(const osqp_batch* b, int32_t i) {

@@ -46,7 +46,9 @@ inline int sched_group(double mean_short, long long nshort, long long nwarps) {
   return std::max(g_min, std::min(g_mean, g_occ));
 }
 
-inline SchedHost make_sched(const std::vector<int>& rp, long long nwarps) {
+// force_group > 0 replaces the rule's group width (the batch autotuner's
+// measured choice).
+inline SchedHost make_sched(const std::vector<int>& rp, long long nwarps, int force_group = 0) {
   SchedHost S;
   const int nrows = (int)rp.size() - 1;
   const long long nnz = nrows > 0 ? rp[nrows] : 0;
@@ -65,7 +67,7 @@ inline SchedHost make_sched(const std::vector<int>& rp, long long nwarps) {
   }
   const long long scount = (long long)shortr.size();
   const double ms = scount ? (double)sn / (double)scount : 1.0;
-  S.group = sched_group(ms, scount, nwarps);
+  S.group = force_group > 0 ? force_group : sched_group(ms, scount, nwarps);
   const int G = S.group, spw = 32 / G;
   std::stable_sort(shortr.begin(), shortr.end(),
                    [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
@@ -191,6 +193,7 @@ inline int check_settings(const osqp_settings& s) {
   if (s.launch < 0 || s.launch > 3) return OSQP_ERR_SETTINGS;
   if (s.polish < 0 || s.polish > 1 || s.polish_refine_iter < 0 || !(s.delta > 0))
     return OSQP_ERR_SETTINGS;
+  if (s.autotune < 0 || s.autotune > 1) return OSQP_ERR_SETTINGS;
   return OSQP_OK;
 }
 

@@ -606,6 +606,7 @@ void osqp_set_default_settings(osqp_settings* s) {
   s->polish = 0;
   s->polish_refine_iter = 3;
   s->delta = 1e-6;
+  s->autotune = 1;
 }
 
 const char* osqp_error_message(int32_t code) {

@@ -8,7 +8,9 @@ is an independent stream, so requests that arrive while others are on the
 GPU start as soon as CTAs free up and their work overlaps on the device —
 as long as the device footprint of the work in flight stays within a budget.
 Large problems (solved by clusters of CTAs, see osqp_batch_uses_cluster)
-are launched alone on their slot.
+are launched alone on their slot, at most `large_slots` of them at a time,
+so that the other slots stay free for small requests, which a launch takes
+in arrival order up to `max_batch` (no cap by default).
 A problem ID has at most one request in flight; later requests for it wait.
 Host-side bookkeeping only: every numeric step runs in the library.
 """
@@ -53,15 +55,20 @@ class RunStats:
     max_inflight_bytes: int
     launches: int
     dropped: int = 0
+    host_launch_s: float = 0.0   # host time inside osqp_batch_launch
+    host_result_s: float = 0.0   # host time reading results (osqp_batch_get)
 
 
 class Server:
     def __init__(self, qps, slots: int = 4, footprint_budget: int | None = None,
-                 stream: int | None = None, prime: bool = True, **settings):
+                 stream: int | None = None, prime: bool = True, large_slots: int | None = None,
+                 **settings):
         if not 1 <= slots <= B.OSQP_BATCH_MAX_SLOTS:
             raise ValueError(f"slots must be in 1..{B.OSQP_BATCH_MAX_SLOTS}")
         self.qps = qps
         self.slots = slots
+        # slots that large requests may hold at once (the rest serve small ones)
+        self.large_slots = max(1, slots // 2) if large_slots is None else max(1, large_slots)
         self.bs = BatchSolver(qps, stream=stream, **settings)
         self.h = self.bs.handle
         self.footprint = [B.osqp_batch_footprint(self.h, i) for i in range(len(qps))]
@@ -87,6 +94,8 @@ class Server:
         pending = collections.deque()
         free = list(range(self.slots))[::-1]
         busy = {}
+        busy_large = 0
+        host_launch = host_result = 0.0
         inflight_ids = set()
         inflight_bytes = 0
         max_inflight = 0
@@ -117,6 +126,9 @@ class Server:
                             r.x = x
                         inflight_ids.discard(r.pid)
                         inflight_bytes -= self.footprint[r.pid]
+                    host_result += clock() - t0 - t_done
+                    if len(busy[slot]) == 1 and self.large[busy[slot][0].pid]:
+                        busy_large -= 1
                     done += len(busy[slot])
                     del busy[slot]
                     free.append(slot)
@@ -127,7 +139,8 @@ class Server:
                     if r.pid in inflight_ids or r.pid in ids:
                         continue
                     if self.large[r.pid]:
-                        if take:
+                        # alone on its slot, and only while a large slot is free
+                        if take or busy_large >= self.large_slots:
                             continue
                         if inflight_bytes + self.footprint[r.pid] > self.budget and inflight_bytes:
                             continue
@@ -147,8 +160,12 @@ class Server:
                     taken = set(id(r) for r in take)
                     pending = collections.deque(r for r in pending if id(r) not in taken)
                     slot = free.pop()
+                    t_h = clock()
                     B.osqp_batch_launch(self.h, slot, [r.pid for r in take], [r.q for r in take],
                                         [r.l for r in take], [r.u for r in take])
+                    host_launch += clock() - t_h
+                    if len(take) == 1 and self.large[take[0].pid]:
+                        busy_large += 1
                     t_l = clock() - t0
                     for r in take:
                         r.t_launch = t_l
@@ -166,7 +183,7 @@ class Server:
         queue = np.array([r.t_launch - r.t_arrival for r in served]) if served else np.zeros(1)
         return RunStats(len(served), wall, len(served) / wall, 1e3 * float(np.percentile(lat, 50)),
                         1e3 * float(np.percentile(lat, 99)), 1e3 * float(queue.mean()),
-                        max_inflight, launches, len(reqs) - len(served))
+                        max_inflight, launches, len(reqs) - len(served), host_launch, host_result)
 
     def close(self):
         self.bs.close()
@@ -194,3 +211,12 @@ def poisson_requests(qps, rate: float, duration: float, seed: int = 0, perturb: 
         q, l, u = perturb_vectors(rng, qps[pid], perturb)
         out.append(Request(pid, t, q, l, u))
     return out
+
+
+def shard_requests(requests, mine):
+    """The requests of a global stream that name this rank's problem IDs
+    (`mine`, global indices as returned by dist.shard), renumbered to the
+    rank's local problem list; arrival times and vectors unchanged."""
+    local_of = {g: k for k, g in enumerate(mine)}
+    return [Request(local_of[r.pid], r.t_arrival, r.q, r.l, r.u) for r in requests
+            if r.pid in local_of]

@@ -140,3 +140,44 @@ def test_two_rank_sharded_solve(tmp_path, oracle_mod):
         assert np.array_equal(np.asarray(merged[i]), ref)
     t, c = map(float, open(tmp_path / "reduced.txt").read().split())
     assert t == 2.0 and c == 10.0
+
+
+def _serve_worker(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    from paper_1711_08013_gb300.serve import poisson_requests, shard_requests
+    D.init("gloo")
+    qps = [pb.random_qp(n, seed=500 + n) for n in (4, 6, 9, 12, 5, 7)]
+    weights = [q.A.nnz for q in qps]
+    mine = D.shard(weights, rank, world)
+    reqs = poisson_requests(qps, rate=3000.0, duration=0.02, seed=5)
+    local = shard_requests(reqs, mine)
+    rows = [(mine[r.pid], r.t_arrival, float(r.q.sum())) for r in local]
+    for part_rank, part in enumerate(D.gather_objects(rows)):
+        if rank == 0:
+            with open(os.path.join(out_dir, f"serve{part_rank}.txt"), "w") as f:
+                for g, t, qs in part:
+                    f.write(f"{g} {t!r} {qs!r}\n")
+    import torch.distributed as dist
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_serving_shards_one_request_stream(tmp_path):
+    """The serving path of bench.py at two ranks: one pool of problem IDs
+    split by LPT, one global request stream filtered by each rank to its IDs;
+    the two local streams are disjoint and together are exactly the global
+    stream (same IDs, arrival times and perturbed vectors)."""
+    from paper_1711_08013_gb300.serve import poisson_requests
+    port = _free_port()
+    mp.spawn(_serve_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    got = []
+    for r in range(2):
+        for line in open(tmp_path / f"serve{r}.txt"):
+            g, t, qs = line.split()
+            got.append((int(g), float(t), float(qs)))
+    qps = [pb.random_qp(n, seed=500 + n) for n in (4, 6, 9, 12, 5, 7)]
+    ref = [(r.pid, r.t_arrival, float(r.q.sum()))
+           for r in poisson_requests(qps, rate=3000.0, duration=0.02, seed=5)]
+    assert len(ref) > 20
+    assert sorted(got) == sorted(ref)

@@ -45,26 +45,56 @@ def test_batch_against_oracle(oracle_mod, precision):
 
 @pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
 def test_batch_result_same_alone_and_in_mix(precision):
+    """With the rule's row partition (autotune = 0) a problem's arithmetic,
+    long rows included (chunk partials summed in chunk order), does not
+    depend on the other problems of the batch: bit-identical results alone
+    and in the mix.  (With the autotuner the partition of a shape class is a
+    measured choice, which two batches may make differently.)"""
     qps = mixed_batch()
-    with BatchSolver(qps, precision=precision) as bs:
+    with BatchSolver(qps, precision=precision, autotune=0) as bs:
         bs.solve()
         mix = [bs.result(i) for i in range(len(qps))]
-    # MPC problems have no row above the long-row threshold: their arithmetic
-    # order is fixed and the results are bit-identical.  The portfolio has a
-    # 300-entry row whose chunk partials are added atomically, so only
-    # rounding-level agreement holds there.
-    for i, exact in ((0, True), (5, True), (len(qps) - 4, False), (len(qps) - 1, True)):
-        with BatchSolver([qps[i]], precision=precision) as one:
+    for i in (0, 5, len(qps) - 4, len(qps) - 1):
+        with BatchSolver([qps[i]], precision=precision, autotune=0) as one:
             one.solve()
             alone = one.result(0)
         assert alone.status == mix[i].status
-        if exact:
-            assert alone.iter == mix[i].iter
-            assert np.array_equal(alone.x, mix[i].x), qps[i].name
-            assert np.array_equal(alone.y, mix[i].y), qps[i].name
-        else:
-            tol = 1e-4 if precision == B.FP32_MIXED else 1e-8
-            assert np.allclose(alone.x, mix[i].x, rtol=tol, atol=tol), qps[i].name
+        assert alone.iter == mix[i].iter
+        assert np.array_equal(alone.x, mix[i].x), qps[i].name
+        assert np.array_equal(alone.y, mix[i].y), qps[i].name
+
+
+GROUPS = [1, 2, 4, 8, 16, 32]
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.FP32_MIXED], ids=["fp64", "fp32"])
+def test_autotuner_uses_the_fastest_measured_partition(oracle_mod, precision):
+    """The batch autotuner times every candidate group width on one matrix
+    of each shape class and gives each class its fastest; the representative
+    problems carry the chosen widths, and the tuned batch's results pass the
+    acceptance test and lie in the convexity interval around the oracle's
+    optimum, like the rule's."""
+    qps = pb.mpc_batch(48, seed=3300) + mixed_batch()[12:]
+    with BatchSolver(qps, precision=precision) as bs:
+        table = B.osqp_batch_tuning(bs.handle)
+        assert len(table) >= 2
+        for kind, rb, mb, xb, rep, chosen, cyc in table:
+            assert np.all(cyc > 0)
+            assert chosen == GROUPS[int(np.argmin(cyc))], (kind, rb, mb, xb, cyc)
+            assert B.osqp_batch_schedule(bs.handle, rep)[kind] == chosen
+        bs.solve()
+        res = [bs.result(i) for i in range(len(qps))]
+    with BatchSolver(qps, precision=precision, autotune=0) as rule:
+        assert B.osqp_batch_tuning(rule.handle) == []
+    for qp, g in zip(qps, res):
+        star = oracle_mod.solve(qp, **HIGH_ORACLE)
+        assert g.status == B.SOLVED, (qp.name, g.status)
+        prim, dual, ep, ed = acceptance(qp, g.x, g.y, 1e-3, 1e-3)
+        assert prim <= ep * 1.01 and dual <= ed * 1.01, (qp.name, prim, ep, dual, ed)
+        lo, hi = objective_interval(qp, g.x, g.z, g.y, star.x, star.y)
+        d = objective(qp, g.x) - star.obj_val
+        slack = 1e-7 * max(1.0, abs(star.obj_val))
+        assert lo - slack <= d <= hi + slack, (qp.name, lo, d, hi)
 
 
 def test_batch_matches_single_problem_solver(oracle_mod):

@@ -148,3 +148,30 @@ def test_requests_with_wrong_vector_lengths_are_refused(monkeypatch):
     with pytest.raises(ValueError, match="q has"):
         srv.run([good, bad], clock=fake_clock(1e-3))
     assert be.launched == []          # refused before anything ran
+
+
+def test_large_requests_leave_slots_for_small_ones(monkeypatch):
+    """With many large (cluster) requests pending, at most large_slots of
+    them hold a slot at any time, so small requests keep being launched on
+    the other slots instead of waiting behind them."""
+    nprob, slots = 10, 4
+    srv, be, _ = make_server(monkeypatch, nprob, slots, None, (0, 1, 2, 3, 4), None, 6, seed=9)
+    srv.large_slots = 1
+    seen = []
+    orig = be.osqp_batch_launch
+
+    def launch(h, slot, pids, qs, ls, us):
+        orig(h, slot, pids, qs, ls, us)
+        running_large = sum(1 for v in be.running.values() if be.lg[v[0][0]] and len(v[0]) == 1)
+        seen.append(running_large)
+
+    be.osqp_batch_launch = launch
+    reqs = [serve.Request(p, 0.0) for p in range(5)] + [serve.Request(5 + k % 5, 0.0005 * k)
+                                                        for k in range(20)]
+    st = srv.run(reqs, clock=fake_clock(1e-3))
+    assert st.requests == len(reqs)
+    assert max(seen) <= 1
+    # small requests were launched while large ones were still waiting
+    first_small = min(i for i, (_, pids) in enumerate(be.launched) if not be.lg[pids[0]])
+    last_large = max(i for i, (_, pids) in enumerate(be.launched) if be.lg[pids[0]])
+    assert first_small < last_large
