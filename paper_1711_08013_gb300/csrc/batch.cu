@@ -79,7 +79,7 @@ __device__ void batch_solve_one(Team& tm, const Dev<T>& d, const Params& P, int 
 // CTA per problem; the problem's vectors fit in `pool`).
 template <typename T>
 __device__ void batch_solve_one_smem(BlockTeam& tm, const Dev<T>& d, const Params& P, int md,
-                                     Dev<T>& sd, unsigned char* pool) {
+                                     Dev<T>& sd, unsigned char* pool, bool with_mat) {
   const double rho_bar = d.sc->rho_bar;
   if (md & kModeScale) {
     if (!scale_stage(tm, d, P, rho_bar, true)) return;
@@ -103,7 +103,7 @@ __device__ void batch_solve_one_smem(BlockTeam& tm, const Dev<T>& d, const Param
       }
     }
   }
-  stage_in(d, sd, pool);
+  stage_in(d, sd, pool, with_mat);
   admm_stage(tm, sd, P);
   stage_out(d, sd);
 }
@@ -128,8 +128,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     const int p = code & ((1 << kModeShift) - 1);
     const Dev<T>& d = devs[p];
     const unsigned long long t0 = gtimer();
-    if (smem_vec_bytes<T>(d.n, d.m) <= (size_t)pool_bytes)
-      batch_solve_one_smem(tm, d, P, code >> kModeShift, sdev, pool);
+    const int plan = smem_plan(d, (size_t)pool_bytes);
+    if (plan > 0)
+      batch_solve_one_smem(tm, d, P, code >> kModeShift, sdev, pool, plan == 2);
     else
       batch_solve_one(tm, d, P, code >> kModeShift);
     __syncthreads();
@@ -443,6 +444,8 @@ void fill_batch_devs(osqp_batch* b) {
     };
     d->kn = sched(L.kn_s, o.kn, L.n);
     d->as = sched(L.a_s, o.a, L.m);
+    d->kn.npos = L.kn_s.npos;
+    d->as.npos = L.a_s.npos;
     dynamic_carve<T>(L, b->arena + L.v_off, d);
   }
 }
@@ -707,6 +710,7 @@ int autotune_groups(osqp_batch* b, const std::vector<HostStructure>& hs) {
                 (const int*)(dbuf + o.li),
                 (double*)(dbuf + o.cp),
                 (unsigned*)(dbuf + o.cc)};
+    t.S.npos = c.S.npos;
     t.ci = (const int*)(dbuf + o.ci);
     t.va = (const T*)(dbuf + o.va);
     t.xg = (T*)(dbuf + o.xg);
@@ -869,38 +873,16 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
   if (cudaGetDevice(&b->device) != cudaSuccess) return fail(OSQP_ERR_CUDA);
   if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
     return fail(OSQP_ERR_CUDA);
-  // Shared memory for the PCG vectors of one problem: the largest need of
-  // the batch, capped (problems above the cap keep their vectors in HBM).
-  {
-    size_t need = 0;
-    for (int i = 0; i < count; ++i) {
-      const size_t v = settings->precision == OSQP_PRECISION_FP64
-                           ? smem_vec_bytes<double>(P[i].n_cols, A[i].n_rows)
-                           : smem_vec_bytes<float>(P[i].n_cols, A[i].n_rows);
-      if (v <= kPoolCap) need = std::max(need, v);
-    }
-    b->pool = (int)need;
-    // the attribute is the cap for every batch (a per-batch value would race
-    // with other batches' launches)
-    const cudaError_t ea =
-        settings->precision == OSQP_PRECISION_FP64
-            ? cudaFuncSetAttribute(k_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kPoolCap)
-            : cudaFuncSetAttribute(k_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kPoolCap);
-    if (ea != cudaSuccess) {
-      cudaGetLastError();
-      b->pool = 0;
-    }
-  }
-  int occ = 0;
-  cudaError_t e = settings->precision == OSQP_PRECISION_FP64
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<double>,
-                                                                      kBatchThreads, b->pool)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<float>,
-                                                                      kBatchThreads, b->pool);
-  if (e != cudaSuccess) return fail(OSQP_ERR_CUDA);
-  b->grid = b->num_sms * std::max(1, occ);
+  // the attribute is the cap for every batch (a per-batch value would race
+  // with other batches' launches)
+  if ((settings->precision == OSQP_PRECISION_FP64
+           ? cudaFuncSetAttribute(k_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kPoolCap)
+           : cudaFuncSetAttribute(k_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kPoolCap)) != cudaSuccess)
+    return fail(OSQP_ERR_CUDA);
+  cudaError_t e = cudaSuccess;
+  b->grid = b->num_sms;  // one persistent CTA per SM (set from the occupancy below)
 
   // Structure of every problem, its schedule and its place in the arena:
   // all static blocks first (one upload), then all dynamic blocks.
@@ -928,6 +910,22 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
     s_total += static_offsets(L).end;
   }
   b->static_bytes = s_total;
+  // Shared memory of a one-CTA solve: the largest need of the batch, capped;
+  // a problem's PCG vectors, and its matrices too when they fit beside them
+  // (problems above the cap keep their vectors in HBM).
+  {
+    size_t need = 0;
+    for (int i = 0; i < count; ++i) {
+      const ProblemLayout& L = b->L[i];
+      const bool f64 = settings->precision == OSQP_PRECISION_FP64;
+      const size_t v = f64 ? smem_vec_bytes<double>(L.n, L.m) : smem_vec_bytes<float>(L.n, L.m);
+      const size_t mb = f64 ? smem_mat_bytes<double>(L.kn_s.npos, L.a_s.npos)
+                            : smem_mat_bytes<float>(L.kn_s.npos, L.a_s.npos);
+      if (v + mb <= kPoolCap) need = std::max(need, v + mb);
+      else if (v <= kPoolCap) need = std::max(need, v);
+    }
+    b->pool = (int)need;
+  }
   size_t v_total = s_total;
   for (int i = 0; i < count; ++i) {
     b->L[i].v_off = v_total;
@@ -936,6 +934,16 @@ int32_t osqp_batch_setup(osqp_batch** out, int32_t count, const osqp_csc* P, con
                    : dynamic_carve<float>(b->L[i], nullptr, nullptr);
   }
   b->arena_bytes = v_total;
+  {
+    int occ = 0;
+    e = settings->precision == OSQP_PRECISION_FP64
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<double>, kBatchThreads,
+                                                            b->pool)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<float>, kBatchThreads,
+                                                            b->pool);
+    if (e != cudaSuccess) return fail(OSQP_ERR_CUDA);
+    b->grid = b->num_sms * std::max(1, occ);
+  }
   const size_t dev_bytes = (settings->precision == OSQP_PRECISION_FP64 ? sizeof(Dev<double>)
                                                                        : sizeof(Dev<float>)) *
                            (size_t)count;

@@ -71,6 +71,7 @@ struct Sched {
   double* cpart;        // per chunk: kMaxNV partial values of the current product
   unsigned* ccount;     // per long row: chunks stored in the current product
                         // (zero between products: the completing warp resets it)
+  int npos;             // positions of the layout (nonzeros and padding)
 };
 
 struct Barrier {
@@ -1221,8 +1222,28 @@ __host__ __device__ constexpr size_t smem_vec_bytes(int n, int m) {
          4 * align16((size_t)m * sizeof(T));
 }
 
+// Column indices and working values of both matrices, when they fit beside
+// the vectors (small problems): the products then read shared memory only.
 template <typename T>
-__device__ void stage_in(const Dev<T>& d, Dev<T>& sd, unsigned char* pool) {
+__host__ __device__ constexpr size_t smem_mat_bytes(int npos_kn, int npos_a) {
+  return align16((size_t)npos_kn * sizeof(int)) + align16((size_t)npos_kn * sizeof(T)) +
+         align16((size_t)npos_a * sizeof(int)) + align16((size_t)npos_a * sizeof(T));
+}
+
+// Copy of `bytes` (a multiple of 4, both pointers 16-byte aligned) by one
+// CTA, 16 bytes per thread and step, then the last words.
+__device__ __forceinline__ void cta_copy(void* dst, const void* src, size_t bytes) {
+  const size_t n16 = bytes / 16;
+  const int4* s4 = reinterpret_cast<const int4*>(src);
+  int4* d4 = reinterpret_cast<int4*>(dst);
+  for (size_t k = threadIdx.x; k < n16; k += blockDim.x) d4[k] = s4[k];
+  const int* s1 = reinterpret_cast<const int*>(src);
+  int* d1 = reinterpret_cast<int*>(dst);
+  for (size_t k = 4 * n16 + threadIdx.x; k < bytes / 4; k += blockDim.x) d1[k] = s1[k];
+}
+
+template <typename T>
+__device__ void stage_in(const Dev<T>& d, Dev<T>& sd, unsigned char* pool, bool with_mat) {
   if (threadIdx.x == 0) {
     sd = d;
     size_t off = 0;
@@ -1237,6 +1258,17 @@ __device__ void stage_in(const Dev<T>& d, Dev<T>& sd, unsigned char* pool) {
     sd.ut1 = take(d.n + d.m);
     T** mv[] = {&sd.ap, &sd.dzt, &sd.rhoT, &sd.rho_invT};
     for (T** q : mv) *q = take(d.m);
+    if (with_mat) {
+      auto take_i = [&](int count) {
+        int* q = reinterpret_cast<int*>(pool + off);
+        off += align16((size_t)count * sizeof(int));
+        return q;
+      };
+      sd.kn_ci = take_i(d.kn.npos);
+      sd.kn_v = take(d.kn.npos);
+      sd.a_ci = take_i(d.as.npos);
+      sd.a_v = take(d.as.npos);
+    }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < d.n; j += blockDim.x) sd.dinv[j] = d.dinv[j];
@@ -1244,7 +1276,22 @@ __device__ void stage_in(const Dev<T>& d, Dev<T>& sd, unsigned char* pool) {
     sd.rhoT[i] = d.rhoT[i];
     sd.rho_invT[i] = d.rho_invT[i];
   }
+  if (with_mat) {
+    cta_copy((void*)sd.kn_ci, d.kn_ci, (size_t)d.kn.npos * sizeof(int));
+    cta_copy((void*)sd.kn_v, d.kn_v, (size_t)d.kn.npos * sizeof(T));
+    cta_copy((void*)sd.a_ci, d.a_ci, (size_t)d.as.npos * sizeof(int));
+    cta_copy((void*)sd.a_v, d.a_v, (size_t)d.as.npos * sizeof(T));
+  }
   __syncthreads();
+}
+
+// What a one-CTA solve of this problem keeps in a pool of pool_bytes:
+// 2 = vectors and matrices, 1 = vectors only, 0 = nothing.
+template <typename T>
+__device__ __forceinline__ int smem_plan(const Dev<T>& d, size_t pool_bytes) {
+  const size_t v = smem_vec_bytes<T>(d.n, d.m);
+  if (v > pool_bytes) return 0;
+  return v + smem_mat_bytes<T>(d.kn.npos, d.as.npos) <= pool_bytes ? 2 : 1;
 }
 
 template <typename T>

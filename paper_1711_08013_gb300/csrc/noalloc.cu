@@ -411,6 +411,7 @@ __device__ bool build_sliced(Sched& S, const NaSched& B, NaPtrs<T>& sp, int nrow
       S.lidx = B.lidx;
       S.cpart = B.cpart;
       S.ccount = B.ccount;
+      S.npos = p;
     }
   }
   __syncthreads();

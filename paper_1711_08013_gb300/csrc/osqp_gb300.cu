@@ -99,8 +99,8 @@ OSQP_CLUSTER_KERNEL(k_scale_cluster, scale_stage(tm, d, P, rho_bar, reset != 0),
 OSQP_CLUSTER_KERNEL(k_refresh_cluster, refresh_stage(tm, d, P, rho_bar), double rho_bar)
 #undef OSQP_CLUSTER_KERNEL
 
-// One-CTA solve; with pool_bytes > 0 the PCG vectors live in the CTA's
-// shared memory (pool_bytes ≥ smem_vec_bytes of the problem).
+// One-CTA solve; with a pool the PCG vectors, and the matrices when they fit
+// too, live in the CTA's shared memory (smem_plan).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_admm_block(const __grid_constant__ Dev<T> d,
                                                           const __grid_constant__ Params P,
@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(kThreads) k_admm_block(const __grid_constant__
   __shared__ Dev<T> sdev;
   extern __shared__ __align__(16) unsigned char pool[];
   BlockTeam tm{sm};
-  if (pool_bytes > 0) {
-    stage_in(d, sdev, pool);
+  const int plan = smem_plan(d, (size_t)pool_bytes);
+  if (plan > 0) {
+    stage_in(d, sdev, pool, plan == 2);
     admm_stage(tm, sdev, P);
     stage_out(d, sdev);
   } else {
@@ -258,6 +259,7 @@ void take_sched(Arena& A, const SchedHost& h, int nrows, Sched& S) {
   S.lidx = A.take<int>(h.lidx.size());
   S.cpart = A.take<double>(h.chunks.size() * kMaxNV);
   S.ccount = A.take<unsigned>(h.lrange.size());
+  S.npos = h.npos;
 }
 
 template <typename T>
@@ -716,9 +718,24 @@ int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const 
     while (per_sm > 1 && s->num_sms * per_sm > 512) --per_sm;
   }
   s->grid = s->num_sms * per_sm;
+  {
+    const long long nwarps =
+        (long long)(s->use_grid ? s->grid : (s->use_cluster ? kClusterSize : 1)) * (kThreads / 32);
+    s->kn_s = make_sched(s->kn_rp, nwarps);
+    s->a_s = make_sched(s->a_rp, nwarps);
+    s->kn_ci = to_positions(s->kn_s, s->kn_ci, -1);
+    s->kn_src = to_positions(s->kn_s, s->kn_src, -1);
+    s->a_ci = to_positions(s->a_s, s->a_ci, -1);
+    s->a_src = to_positions(s->a_s, s->a_src, -1);
+    s->kn_s.pos = {};
+    s->a_s.pos = {};
+  }
   if (!s->use_grid && !s->use_cluster) {
-    const size_t need = settings->precision == OSQP_PRECISION_FP64 ? smem_vec_bytes<double>(n, m)
-                                                                   : smem_vec_bytes<float>(n, m);
+    const bool f64 = settings->precision == OSQP_PRECISION_FP64;
+    const size_t v = f64 ? smem_vec_bytes<double>(n, m) : smem_vec_bytes<float>(n, m);
+    const size_t mb = f64 ? smem_mat_bytes<double>(s->kn_s.npos, s->a_s.npos)
+                          : smem_mat_bytes<float>(s->kn_s.npos, s->a_s.npos);
+    const size_t need = v + mb <= kBlockPoolCap ? v + mb : v;
     if (need <= kBlockPoolCap) {
       // the attribute is the cap for every solver (a per-solver value would
       // race with other solvers' launches)
@@ -731,18 +748,6 @@ int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const 
       if (ea == cudaSuccess) s->pool = (int)need;
       else cudaGetLastError();
     }
-  }
-  {
-    const long long nwarps =
-        (long long)(s->use_grid ? s->grid : (s->use_cluster ? kClusterSize : 1)) * (kThreads / 32);
-    s->kn_s = make_sched(s->kn_rp, nwarps);
-    s->a_s = make_sched(s->a_rp, nwarps);
-    s->kn_ci = to_positions(s->kn_s, s->kn_ci, -1);
-    s->kn_src = to_positions(s->kn_s, s->kn_src, -1);
-    s->a_ci = to_positions(s->a_s, s->a_ci, -1);
-    s->a_src = to_positions(s->a_s, s->a_src, -1);
-    s->kn_s.pos = {};
-    s->a_s.pos = {};
   }
   const size_t part_doubles = (size_t)2 * s->grid * kMaxRed;
   const size_t bytes = settings->precision == OSQP_PRECISION_FP64
