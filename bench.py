@@ -458,21 +458,17 @@ def batch_main(args, ws, rank, local):
     t_launch = statistics.mean(step_s)
     peak, peak_src = hbm_peak()
     # end to end through the public API: new q/l/u of every problem from
-    # pinned host memory, the solve, and x, y of every problem back to the host
-    pins = [(torch.tensor(q.q).pin_memory(), torch.tensor(q.l).pin_memory(),
-             torch.tensor(q.u).pin_memory()) for q in qps]
-    outs = [(torch.empty(q.n, dtype=torch.float64).pin_memory(),
-             torch.empty(q.m, dtype=torch.float64).pin_memory()) for q in qps]
-    L = B.lib()
+    # pinned host memory (one whole-batch transfer per vector), the solve,
+    # and x, y of every problem back to pinned host memory
+    cat = lambda vs: torch.tensor(np.concatenate(vs)).pin_memory()
+    q_all, l_all, u_all = cat([q.q for q in qps]), cat([q.l for q in qps]), cat([q.u for q in qps])
+    x_all = torch.empty(sum(q.n for q in qps), dtype=torch.float64).pin_memory()
+    y_all = torch.empty(sum(q.m for q in qps), dtype=torch.float64).pin_memory()
 
     def e2e_step():
-        for i, (a, b_, c) in enumerate(pins):
-            if L.osqp_batch_update_vectors(h, i, a.data_ptr(), b_.data_ptr(), c.data_ptr()) != 0:
-                raise SystemExit("update failed")
+        B.osqp_batch_update_all(h, q_all.data_ptr(), l_all.data_ptr(), u_all.data_ptr())
         B.osqp_batch_solve(h)
-        for i, (xo, yo) in enumerate(outs):
-            if L.osqp_batch_get(h, i, xo.data_ptr(), yo.data_ptr(), None, None) != 0:
-                raise SystemExit("get failed")
+        B.osqp_batch_get_all(h, x_all.data_ptr(), y_all.data_ptr())
 
     e2e_step()
     e2e_steps = max(1, min(args.steps, 3))

@@ -249,6 +249,23 @@ int32_t osqp_batch_reset(osqp_batch* b);
 int32_t osqp_batch_update_vectors(osqp_batch* b, int32_t i, const double* q, const double* l,
                                   const double* u);
 
+/* §6 vectors as parameters for every problem at once: q_all (Σ n_i values),
+ * l_all and u_all (Σ m_i values each), concatenated in problem order (host
+ * arrays; q_all may be NULL = unchanged, l_all and u_all are both given or
+ * both NULL).  Validated on the host like osqp_batch_update_vectors, copied
+ * with one transfer per array into a device staging buffer (allocated by
+ * the first whole-batch call) and scattered on the device; every problem
+ * warm-starts at the next solve.  Enqueued on the batch's stream (page-locked
+ * arrays keep the copies asynchronous).  OSQP_ERR_ARG while a slot launch
+ * is in flight. */
+int32_t osqp_batch_update_all(osqp_batch* b, const double* q_all, const double* l_all,
+                              const double* u_all);
+
+/* Unscaled x (Σ n_i) and y (Σ m_i) of every problem, concatenated in problem
+ * order (host arrays, either may be NULL): gathered on the device and copied
+ * with one transfer per array.  Waits for in-flight slots and the stream. */
+int32_t osqp_batch_get_all(osqp_batch* b, double* x_all, double* y_all);
+
 /* Unscaled x (n_i), y (m_i), z (m_i) of problem i (host arrays, any may be
  * NULL) and its info (solve_time = that problem's device time inside the
  * last launch, setup_time = the whole launch's device time).  Waits for the

@@ -94,6 +94,8 @@ _SIGS = {
     "osqp_batch_slot_wait": (C.c_int32, [_P, C.c_int32]),
     "osqp_batch_footprint": (C.c_int64, [_P, C.c_int32]),
     "osqp_batch_schedule": (C.c_int32, [_P, C.c_int32, _P]),
+    "osqp_batch_update_all": (C.c_int32, [_P, _P, _P, _P]),
+    "osqp_batch_get_all": (C.c_int32, [_P, _P, _P]),
     "osqp_batch_tuning": (C.c_int32, [_P, C.c_int32, _P, _P]),
 }
 OSQP_BATCH_MAX_SLOTS = 32
@@ -369,3 +371,19 @@ def osqp_batch_tuning(h):
     lib().osqp_batch_tuning(h, n, _ptr(info), _ptr(cyc))
     return [tuple(int(v) for v in info[6 * k:6 * k + 6]) + (cyc[6 * k:6 * k + 6].copy(),)
             for k in range(n)]
+
+
+def osqp_batch_update_all(h, q_all=None, l_all=None, u_all=None):
+    """Concatenated q (Σn), l and u (Σm) of every problem: numpy arrays or
+    host addresses (ints, e.g. pinned tensors)."""
+    arrs = [None if v is None or isinstance(v, int) else np.ascontiguousarray(v, np.float64)
+            for v in (q_all, l_all, u_all)]
+    ptrs = [v if isinstance(v, int) else _ptr(a) for v, a in zip((q_all, l_all, u_all), arrs)]
+    _check(lib().osqp_batch_update_all(h, *ptrs), "osqp_batch_update_all")
+
+
+def osqp_batch_get_all(h, x_all, y_all):
+    """Fill host arrays (numpy, or int addresses) with every problem's x, y."""
+    _check(lib().osqp_batch_get_all(h, x_all if isinstance(x_all, int) else _ptr(x_all),
+                                    y_all if isinstance(y_all, int) else _ptr(y_all)),
+           "osqp_batch_get_all")

@@ -240,6 +240,39 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   if (threadIdx.x == 0) *c.cycles = (unsigned long long)(t1 - t0);
 }
 
+// Whole-batch vector transfers: one CTA per problem moves its segment of
+// the concatenated vectors.  Scatter: stage → raw q, l, u (each may be
+// absent).  Gather: unscaled x, y → stage.
+template <typename T>
+__global__ void k_scatter_vectors(const Dev<T>* __restrict__ devs, int count,
+                                  const long long* __restrict__ off, const double* __restrict__ q,
+                                  const double* __restrict__ l, const double* __restrict__ u) {
+  const long long* off_n = off;
+  const long long* off_m = off + count + 1;
+  for (int p = blockIdx.x; p < count; p += gridDim.x) {
+    const Dev<T>& d = devs[p];
+    for (int j = threadIdx.x; j < d.n; j += blockDim.x)
+      if (q) const_cast<double*>(d.q_raw)[j] = q[off_n[p] + j];
+    for (int i = threadIdx.x; i < d.m; i += blockDim.x) {
+      if (l) const_cast<double*>(d.l_raw)[i] = l[off_m[p] + i];
+      if (u) const_cast<double*>(d.u_raw)[i] = u[off_m[p] + i];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_gather_solutions(const Dev<T>* __restrict__ devs, int count,
+                                   const long long* __restrict__ off, double* __restrict__ x,
+                                   double* __restrict__ y) {
+  const long long* off_n = off;
+  const long long* off_m = off + count + 1;
+  for (int p = blockIdx.x; p < count; p += gridDim.x) {
+    const Dev<T>& d = devs[p];
+    for (int j = threadIdx.x; j < d.n; j += blockDim.x) x[off_n[p] + j] = d.x_out[j];
+    for (int i = threadIdx.x; i < d.m; i += blockDim.x) y[off_m[p] + i] = d.y_out[i];
+  }
+}
+
 // Per-problem sizes and offsets.
 struct ProblemLayout {
   int n = 0, m = 0, nnz_kn = 0, nnz_a = 0;
@@ -396,6 +429,12 @@ struct osqp_batch {
   std::vector<int> inflight;        // slot holding problem i, or -1
   std::vector<size_t> footprint;    // device bytes of problem i
   unsigned long long* times_d = nullptr;
+  // whole-batch vector transfers: offsets of problem i in the concatenated
+  // n- and m-vectors (host and device), and a device staging buffer of
+  // Σn + 2Σm values (allocated on first use)
+  std::vector<long long> off_n, off_m;
+  long long* off_d = nullptr;
+  double* stage_d = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   double last_time = 0.0;
   bool solved = false;
@@ -1171,6 +1210,105 @@ int32_t osqp_batch_update_vectors(osqp_batch* b, int32_t i, const double* q, con
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? OSQP_OK : OSQP_ERR_CUDA;
 }
 
+// Offsets of the concatenated vectors and the staging buffer, on first use.
+static int32_t whole_batch_buffers(osqp_batch* b) {
+  if (b->stage_d) return OSQP_OK;
+  const int count = b->count;
+  b->off_n.assign(count + 1, 0);
+  b->off_m.assign(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    b->off_n[i + 1] = b->off_n[i] + b->L[i].n;
+    b->off_m[i + 1] = b->off_m[i] + b->L[i].m;
+  }
+  std::vector<long long> both(b->off_n);
+  both.insert(both.end(), b->off_m.begin(), b->off_m.end());
+  const size_t vals = (size_t)b->off_n[count] + 2 * (size_t)b->off_m[count];
+  if (cudaMalloc((void**)&b->off_d, sizeof(long long) * both.size()) != cudaSuccess ||
+      cudaMalloc((void**)&b->stage_d, sizeof(double) * std::max<size_t>(vals, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    if (b->off_d) cudaFree(b->off_d);
+    b->off_d = nullptr;
+    b->stage_d = nullptr;
+    return OSQP_ERR_OOM;
+  }
+  if (cudaMemcpy(b->off_d, both.data(), sizeof(long long) * both.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return OSQP_ERR_CUDA;
+  return OSQP_OK;
+}
+
+int32_t osqp_batch_update_all(osqp_batch* b, const double* q_all, const double* l_all,
+                              const double* u_all) {
+  if (!b || ((l_all == nullptr) != (u_all == nullptr))) return OSQP_ERR_ARG;
+  for (int v : b->inflight)
+    if (v >= 0) return OSQP_ERR_ARG;
+  if (!q_all && !l_all) return OSQP_OK;
+  int rc = whole_batch_buffers(b);
+  if (rc) return rc;
+  const long long N = b->off_n[b->count], M = b->off_m[b->count];
+  if (q_all)
+    for (long long j = 0; j < N; ++j)
+      if (!std::isfinite(q_all[j])) return OSQP_ERR_NONFINITE;
+  if (l_all)
+    for (long long r = 0; r < M; ++r) {
+      if (std::isnan(l_all[r]) || std::isnan(u_all[r])) return OSQP_ERR_NONFINITE;
+      if (l_all[r] > u_all[r]) return OSQP_ERR_LGTU;
+    }
+  double* sq = b->stage_d;
+  double* sl = b->stage_d + N;
+  double* su = sl + M;
+  if ((q_all && N && cudaMemcpyAsync(sq, q_all, sizeof(double) * N, cudaMemcpyHostToDevice,
+                                     b->stream) != cudaSuccess) ||
+      (l_all && M && cudaMemcpyAsync(sl, l_all, sizeof(double) * M, cudaMemcpyHostToDevice,
+                                     b->stream) != cudaSuccess) ||
+      (u_all && M && cudaMemcpyAsync(su, u_all, sizeof(double) * M, cudaMemcpyHostToDevice,
+                                     b->stream) != cudaSuccess))
+    return OSQP_ERR_CUDA;
+  const int grid = std::min(b->count, 4 * b->num_sms);
+  if (b->set.precision == OSQP_PRECISION_FP64)
+    k_scatter_vectors<double><<<grid, 256, 0, b->stream>>>((const Dev<double>*)b->devs, b->count,
+                                                           b->off_d, q_all ? sq : nullptr,
+                                                           l_all ? sl : nullptr,
+                                                           u_all ? su : nullptr);
+  else
+    k_scatter_vectors<float><<<grid, 256, 0, b->stream>>>((const Dev<float>*)b->devs, b->count,
+                                                          b->off_d, q_all ? sq : nullptr,
+                                                          l_all ? sl : nullptr,
+                                                          u_all ? su : nullptr);
+  if (cudaGetLastError() != cudaSuccess) return OSQP_ERR_CUDA;
+  for (int i = 0; i < b->count; ++i)
+    if (!(b->mode[i] & kModeScale)) b->mode[i] |= kModeRefresh;
+  return OSQP_OK;
+}
+
+int32_t osqp_batch_get_all(osqp_batch* b, double* x_all, double* y_all) {
+  if (!b) return OSQP_ERR_ARG;
+  for (int v : b->inflight)
+    if (v >= 0) {
+      const int rc = osqp_batch_slot_wait(b, v);
+      if (rc) return rc;
+    }
+  int rc = whole_batch_buffers(b);
+  if (rc) return rc;
+  const long long N = b->off_n[b->count], M = b->off_m[b->count];
+  double* sx = b->stage_d;
+  double* sy = b->stage_d + N;
+  const int grid = std::min(b->count, 4 * b->num_sms);
+  if (b->set.precision == OSQP_PRECISION_FP64)
+    k_gather_solutions<double><<<grid, 256, 0, b->stream>>>((const Dev<double>*)b->devs, b->count,
+                                                            b->off_d, sx, sy);
+  else
+    k_gather_solutions<float><<<grid, 256, 0, b->stream>>>((const Dev<float>*)b->devs, b->count,
+                                                           b->off_d, sx, sy);
+  if (cudaGetLastError() != cudaSuccess) return OSQP_ERR_CUDA;
+  if ((x_all && N && cudaMemcpyAsync(x_all, sx, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                                     b->stream) != cudaSuccess) ||
+      (y_all && M && cudaMemcpyAsync(y_all, sy, sizeof(double) * M, cudaMemcpyDeviceToHost,
+                                     b->stream) != cudaSuccess))
+    return OSQP_ERR_CUDA;
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? OSQP_OK : OSQP_ERR_CUDA;
+}
+
 int32_t osqp_batch_launch(osqp_batch* b, int32_t slot, const int32_t* idx, int32_t k,
                           const double* const* q, const double* const* l, const double* const* u) {
   if (!b || slot < 0 || slot >= OSQP_BATCH_MAX_SLOTS || k < 1 || k > b->count || !idx)
@@ -1345,7 +1483,8 @@ int32_t osqp_batch_cleanup(osqp_batch* b) {
   }
   if (b->cfork) cudaEventDestroy(b->cfork);
   if (b->cjoin) cudaEventDestroy(b->cjoin);
-  void* ptrs[] = {b->arena, b->devs, b->order_d, b->queue, b->times_d, b->corder, b->cqueue,
+  void* ptrs[] = {b->arena, b->devs, b->order_d, b->queue, b->times_d, b->off_d, b->stage_d,
+                  b->corder, b->cqueue,
                   b->cerr};
   for (void* p : ptrs)
     if (p && cudaFree(p) != cudaSuccess) rc = OSQP_ERR_CUDA;

@@ -189,3 +189,38 @@ def test_heavy_problems_on_clusters():
         assert prim <= 1.01 * ep and dual <= 1.01 * ed, i
         if r.launch == 1 and first[i].launch == 1:
             assert np.array_equal(r.x, first[i].x), i
+
+
+
+def test_whole_batch_update_and_read_back_match_per_problem_calls():
+    """osqp_batch_update_all / osqp_batch_get_all (one transfer per vector
+    for the whole batch) give the same solves and solutions as the
+    per-problem update and read-back calls, bit for bit."""
+    qps = mixed_batch()
+    rng = np.random.default_rng(17)
+    new = [pb.perturb_vectors(rng, q) for q in qps]
+    out = []
+    for whole in (True, False):
+        with BatchSolver(qps, autotune=0) as bs:
+            bs.solve()
+            if whole:
+                B.osqp_batch_update_all(bs.handle, np.concatenate([v[0] for v in new]),
+                                        np.concatenate([v[1] for v in new]),
+                                        np.concatenate([v[2] for v in new]))
+            else:
+                for i, v in enumerate(new):
+                    bs.update_vectors(i, *v)
+            bs.solve()
+            x = np.empty(sum(q.n for q in qps))
+            y = np.empty(sum(q.m for q in qps))
+            B.osqp_batch_get_all(bs.handle, x, y)
+            per = [bs.result(i) for i in range(len(qps))]
+            assert np.array_equal(x, np.concatenate([r.x for r in per]))
+            assert np.array_equal(y, np.concatenate([r.y for r in per]))
+            out.append(x)
+    assert np.array_equal(out[0], out[1])
+    with BatchSolver(qps[:2], autotune=0) as bs:
+        bad_l = np.concatenate([new[0][1], new[1][1]])
+        bad_u = bad_l - 1.0
+        with pytest.raises(B.OsqpError):
+            B.osqp_batch_update_all(bs.handle, None, bad_l, bad_u)
