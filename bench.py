@@ -63,8 +63,10 @@ PARAM_LEN = {"lasso_path": 100, "mpc_loop": 100, "portfolio_bt": 960}
 # the dominant kernel, from one ncu capture of the same command with the
 # kernels as they are now; for the batch, the capture of the first 608
 # problems scaled by the problems of the launch.  Absent: not captured
-# since the kernels last changed.
+# since the kernels last changed.  The single-problem figure holds for the
+# row partitions it was captured with (group widths of Kn and Ā).
 TRAFFIC = {("lasso", "fp64"): 19.661056e6}
+TRAFFIC_GROUPS = {("lasso", "fp64"): (2, 2)}
 TRAFFIC_BATCH_PER_PROBLEM = {"fp32": 3.536293e9 / 608}
 # Mean time per QP and mean iterations per QP that the paper reports for the
 # same sequences (OSQP direct method on a CPU; context only)
@@ -84,6 +86,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mpc_batch")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default=None,
                     help="default: fp32 (mixed) for mpc_batch, fp64 otherwise")
+    ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
+                    help="1: row partitions chosen by timing at setup; 0: the row-length rule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true",
                     help="mpc_batch: skip the plain single-problem FP64 Lasso measurement")
@@ -417,7 +421,8 @@ def batch_main(args, ws, rank, local):
     prec = B.FP64 if args.precision == "fp64" else B.FP32_MIXED
     stream = torch.cuda.Stream()
     sb = D.ShardedBatch(weights, lambda i: pb.mpc(*spec[i][:2], seed=spec[i][2]),
-                        lambda qs: BatchSolver(qs, stream=stream.cuda_stream, precision=prec),
+                        lambda qs: BatchSolver(qs, stream=stream.cuda_stream, precision=prec,
+                                               autotune=args.autotune),
                         rank=rank, world=ws)
     qps, bs = sb.problems, sb.solver
     local_count = len(qps)
@@ -818,7 +823,8 @@ def single_main(args, ws, rank, local, init_dist=True):
     cfg, desc, qp = build_problem(args, rank)
     prec = B.FP64 if args.precision == "fp64" else B.FP32_MIXED
     stream = torch.cuda.Stream()
-    s = Solver(qp, stream=stream.cuda_stream, precision=prec)
+    s = Solver(qp, stream=stream.cuda_stream, precision=prec, autotune=args.autotune)
+    groups = B.osqp_diag_schedule(s.handle)
     n, m = qp.n, qp.m
     dev = torch.device("cuda", local)
     Pv = torch.tensor(qp.P.data, dtype=torch.float64, device=dev)
@@ -927,7 +933,11 @@ def single_main(args, ws, rank, local, init_dist=True):
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "eps": 1e-3,
                    "l2": "flushed between steps (256 MB write outside the timed events)",
-                   "parallelism": "replicas" if ws > 1 else "single"},
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "row_groups": {"Kn": groups[0], "A": groups[1],
+                                  "chosen_by": {1: "timing", 0: "rule"}.get(groups[2], "rule (timing failed)"),
+                                  **({"ms_Kn": [round(v, 4) for v in groups[3]],
+                                      "ms_A": [round(v, 4) for v in groups[4]]} if groups[2] == 1 else {})}},
         "admm_iter_per_s": iters_all / total_max,
         "p50_ms": 1e3 * lat[len(lat) // 2],
         "p99_ms": 1e3 * lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))],
@@ -939,7 +949,9 @@ def single_main(args, ws, rank, local, init_dist=True):
                          infos[-1].launch, "k_admm_grid"),
                      "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": TRAFFIC.get((args.workload, args.precision)),
+                     "traffic": (TRAFFIC.get((args.workload, args.precision))
+                                 if TRAFFIC_GROUPS.get((args.workload, args.precision)) == tuple(groups[:2])
+                                 else None),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_launch},
         "e2e": {"value": ws * args.steps / e2e_dt, "unit": UNIT,

@@ -112,9 +112,10 @@ typedef struct {
                                     residuals are no larger.  Default 0 */
   int32_t polish_refine_iter;    /* refinement passes, default 3 */
   double delta;                  /* δ of Eq. (kkt_polish_reg), default 1e-6 */
-  int32_t autotune;              /* batch only: 1 = time the candidate row partitions
-                                    (group widths 1…32) of each shape class of
-                                    matrices at osqp_batch_setup and use the fastest;
+  int32_t autotune;              /* 1 = time the candidate row partitions (group
+                                    widths 1…32) at setup and use the fastest: per
+                                    shape class of matrices in osqp_batch_setup, per
+                                    matrix in osqp_setup on the whole-GPU grid team;
                                     0 = the row-length rule.  Default 1 */
   int32_t pad2;
 } osqp_settings;
@@ -330,6 +331,20 @@ int32_t osqp_batch_cleanup(osqp_batch* b);
  * values read after the solve belong to the final ρ̄).  Returns OSQP_ERR_ARG
  * for a NULL solver, OSQP_ERR_CUDA on a failed copy. */
 int32_t osqp_diag_scaling(osqp_solver* s, double* D, double* E, double* c, double* jacobi);
+
+/* Row partition of a single problem (a schedule choice; the paper has no
+ * counterpart): groups[0], groups[1] = lanes per row (group width G) of the
+ * Kn = [P̄ Āᵀ] and Ā products, groups[2] = 1 when the widths were measured
+ * (settings->autotune on the whole-GPU grid team: every candidate G = 1, 2,
+ * 4, 8, 16, 32 of each matrix timed over 20 products at setup; the fastest
+ * is used unless the rule's width is within 3 % of it), 0 when the
+ * row-length rule chose them, -1 when a CUDA call of the timing failed (the
+ * rule's widths are then in force and the solver works as with autotune = 0).  Widths chosen by timing can differ between
+ * two setups of the same problem, and with them the rounding of the
+ * products; autotune = 0 gives the same arithmetic on every setup.  ms (12 values, may be NULL) receives the
+ * measured milliseconds per timed launch of each candidate, Kn then Ā
+ * (zeros without tuning). */
+int32_t osqp_diag_schedule(osqp_solver* s, int32_t* groups, double* ms);
 
 /* Diagnostic of the bounded grid barrier that every multi-CTA solve relies
  * on (the paper has no counterpart).  Launches four cooperative CTAs on the

@@ -79,6 +79,7 @@ _SIGS = {
     "osqp_cleanup": (C.c_int32, [_P]),
     "osqp_diag_barrier_timeout": (C.c_int32, [C.c_double]),
     "osqp_diag_scaling": (C.c_int32, [_P, _P, _P, _P, _P]),
+    "osqp_diag_schedule": (C.c_int32, [_P, _P, _P]),
     "osqp_batch_uses_cluster": (C.c_int32, [_P, C.c_int32]),
     "osqp_batch_setup": (C.c_int32, [C.POINTER(_P), C.c_int32, _P, _P, _P, _P, _P,
                                      C.POINTER(osqp_settings), _P]),
@@ -387,3 +388,11 @@ def osqp_batch_get_all(h, x_all, y_all):
     _check(lib().osqp_batch_get_all(h, x_all if isinstance(x_all, int) else _ptr(x_all),
                                     y_all if isinstance(y_all, int) else _ptr(y_all)),
            "osqp_batch_get_all")
+
+
+def osqp_diag_schedule(h):
+    """(G of Kn, G of Ā, tuned flag, ms per candidate of Kn (6), of Ā (6))."""
+    g = np.zeros(3, np.int32)
+    ms = np.zeros(12)
+    _check(lib().osqp_diag_schedule(h, _ptr(g), _ptr(ms)), "osqp_diag_schedule")
+    return int(g[0]), int(g[1]), int(g[2]), ms[:6].copy(), ms[6:].copy()

@@ -139,6 +139,48 @@ __global__ void __launch_bounds__(kThreads) k_barrier_probe(Barrier* bar, int* e
   tm.sync();
 }
 
+// Autotuner of a single problem's row partition on the grid team: `reps`
+// products shaped like the PCG loop's (Alg. 1, step 3), each followed by a
+// grid reduction and barrier as in the solve.  KN: w = σu + Kn u with long
+// rows left as chunk partials and the inner product (w, u) reduced; else
+// t = ρ ∘ Ā (D⁻¹ r), the preconditioned residual gathered on the fly.  x and
+// x2 hold ones (x: the gathered vector, x2: the diagonal factor).
+template <typename T, bool KN>
+__global__ void __launch_bounds__(kThreads)
+    k_tune_grid(const __grid_constant__ Sched S, const int* __restrict__ ci,
+                const T* __restrict__ va, const T* __restrict__ x, const T* __restrict__ x2,
+                T* __restrict__ y, int reps, Barrier* bar, int* err, double* part,
+                unsigned long long timeout_ns) {
+  __shared__ double sm[kSmemDoubles];
+  GridTeam tm{bar, err, part, sm, timeout_ns, 0, 0u};
+  for (int r = 0; r < reps; ++r) {
+    T acc1 = T(0);
+    if constexpr (KN) {
+      spmv<1, false, T, T>(
+          tm, S, ci, va, [&](int col, T v, T* acc) { acc[0] += v * x[col]; },
+          [&](int j, T* acc) {
+            const T wj = x2[j] * x[j] + acc[0];
+            y[j] = wj;
+            acc1 += wj * x[j];
+          },
+          [&](int j, int first, T* acc) { acc1 += (acc[0] + (first ? x2[j] : T(0))) * x[j]; },
+          NoLong{}, LazyTag{});
+    } else {
+      spmv<1, false, T, T>(
+          tm, S, ci, va, [&](int col, T v, T* acc) { acc[0] += v * (x[col] * x2[col]); },
+          [&](int i, T* acc) {
+            y[i] = x2[i] * acc[0];
+            acc1 += y[i];
+          });
+    }
+    const T red_t[1] = {acc1};
+    tm.template publish<1, 0u>(red_t);
+    if (!tm.sync()) return;
+    double red[1];
+    tm.template collect<1, 0u>(red);
+  }
+}
+
 // warm start, part 1: x̄ = D⁻¹x, ȳ = cE⁻¹y, x̃ = x̄, δ = 0
 template <typename T>
 __global__ void k_warm_xy(const __grid_constant__ Dev<T> d, const double* __restrict__ xw,
@@ -205,6 +247,11 @@ constexpr size_t kBlockPoolCap = 160 << 10;  // shared memory for a one-CTA solv
 struct osqp_solver {
   int device = 0, num_sms = 0, grid = 0, use_grid = 0, use_cluster = 0;
   int pool = 0;  // dynamic shared memory of the one-CTA solve (0: vectors in HBM)
+  // grid-team autotuner: chosen group widths of Kn and Ā (0: the rule, -1:
+  // the timing failed and the rule is in force) and
+  // the measured milliseconds per launch of each candidate G = 1…32
+  int tuned_kn = 0, tuned_a = 0;
+  double tune_kn_ms[6] = {0, 0, 0, 0, 0, 0}, tune_a_ms[6] = {0, 0, 0, 0, 0, 0};
   cudaStream_t stream = nullptr;
   osqp_settings set{};
   Params P{};
@@ -488,6 +535,121 @@ int check_device_error(osqp_solver* s) {
   return e == kDevOk ? OSQP_OK : OSQP_ERR_DEVICE;
 }
 
+// Group widths tried by the autotuner and its products per timed launch.
+constexpr int kGridTuneGroups[] = {1, 2, 4, 8, 16, 32};
+constexpr int kGridTuneReps = 20;
+constexpr float kGridTuneMargin = 1.03f;
+
+// Time every candidate group width of one matrix (kn: Kn, else Ā; CSR row
+// pointers rp, columns ci, ncols gathered entries) on the grid team, with
+// the product the PCG loop makes of it, and return the one
+// to use: the fastest, unless the rule's width is within kGridTuneMargin of
+// it (timing noise then does not move the choice); -1 when a CUDA call fails
+// (the rule stays in force).  The device memory of each candidate is
+// allocated and freed here, at setup.
+template <typename T>
+int tune_grid_matrix(osqp_solver* s, bool kn, const std::vector<int>& rp,
+                     const std::vector<int>& ci, int ncols, long long nwarps, double* ms_out) {
+  const int nrows = (int)rp.size() - 1;
+  int best = 0;
+  float best_ms = 0.f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return -1;
+  }
+  for (int k = 0; k < 6; ++k) {
+    const int g = kGridTuneGroups[k];
+    ms_out[k] = 0.0;
+    SchedHost h = make_sched(rp, nwarps, g);
+    std::vector<int> cpos = to_positions(h, ci, -1);
+    std::vector<T> vpos(cpos.size());
+    for (size_t q = 0; q < cpos.size(); ++q) vpos[q] = cpos[q] >= 0 ? T(1) : T(0);
+    // arrays of the candidate: one pass over a null arena sizes the
+    // allocation, a second carves it
+    Sched S{};
+    int* d_ci = nullptr;
+    T *d_va = nullptr, *d_x = nullptr, *d_x2 = nullptr, *d_y = nullptr;
+    Barrier* bar = nullptr;
+    int* err = nullptr;
+    double* part = nullptr;
+    auto carve = [&](Arena& A) {
+      take_sched(A, h, nrows, S);
+      d_ci = A.take<int>(h.npos);
+      d_va = A.take<T>(h.npos);
+      d_x = A.take<T>(ncols);
+      d_x2 = A.take<T>(std::max(nrows, ncols));
+      d_y = A.take<T>(nrows);
+      bar = A.take<Barrier>(1);
+      err = A.take<int>(1);
+      part = A.take<double>((size_t)2 * s->grid * kMaxRed);
+    };
+    Arena sizing;
+    carve(sizing);
+    const size_t bytes = sizing.off + 256;
+    char* mem = nullptr;
+    if (cudaMalloc((void**)&mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      best = -1;
+      break;
+    }
+    Arena A{mem, 0};
+    carve(A);
+    std::vector<T> ones(std::max(ncols, 1), T(1)), ones2(std::max(std::max(nrows, ncols), 1), T(1));
+    // host → device copy of a whole vector (nothing to do when it is empty)
+    auto up = [](const void* dst, const auto& v) {
+      return v.empty() || cudaMemcpy(const_cast<void*>(dst), v.data(), sizeof(v[0]) * v.size(),
+                                     cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    bool ok = cudaMemset(mem, 0, bytes) == cudaSuccess && up(d_ci, cpos) && up(d_va, vpos) &&
+              up(d_x, ones) && up(d_x2, ones2) && up(S.slices, h.slices) && up(S.srow, h.srow) &&
+              up(S.chunks, h.chunks) && up(S.long_rows, h.long_rows) && up(S.lrange, h.lrange) &&
+              up(S.lidx, h.lidx);
+    float ms_min = 0.f;
+    for (int pass = 0; ok && pass < 3; ++pass) {
+      // barrier counter and error flag zeroed before every launch
+      int reps = kGridTuneReps;
+      unsigned long long tns = s->P.barrier_timeout_ns;
+      ok = cudaMemsetAsync(bar, 0, sizeof(Barrier), s->stream) == cudaSuccess &&
+           cudaMemsetAsync(err, 0, sizeof(int), s->stream) == cudaSuccess &&
+           cudaEventRecord(e0, s->stream) == cudaSuccess;
+      void* args[] = {(void*)&S,   (void*)&d_ci, (void*)&d_va, (void*)&d_x,
+                      (void*)&d_x2, (void*)&d_y, (void*)&reps, (void*)&bar,
+                      (void*)&err, (void*)&part, (void*)&tns};
+      const void* fn = kn ? (const void*)k_tune_grid<T, true> : (const void*)k_tune_grid<T, false>;
+      ok = ok && cudaLaunchCooperativeKernel(fn, dim3(s->grid), dim3(kThreads), args, 0,
+                                             s->stream) == cudaSuccess;
+      ok = ok && cudaEventRecord(e1, s->stream) == cudaSuccess &&
+           cudaStreamSynchronize(s->stream) == cudaSuccess;
+      int he = 0;
+      ok = ok && cudaMemcpy(&he, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && he == 0;
+      float ms = 0.f;
+      ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      if (ok && pass > 0) ms_min = pass == 1 ? ms : std::min(ms_min, ms);
+    }
+    cudaFree(mem);
+    if (!ok) {
+      cudaGetLastError();
+      best = -1;
+      break;
+    }
+    ms_out[k] = ms_min;
+    if (best == 0 || ms_min < best_ms) {
+      best = g;
+      best_ms = ms_min;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best > 0) {
+    const int rule = make_sched(rp, nwarps).group;
+    for (int k = 0; k < 6; ++k)
+      if (kGridTuneGroups[k] == rule && ms_out[k] <= kGridTuneMargin * best_ms) best = rule;
+  }
+  return best;
+}
+
 int build_structure(osqp_solver* s, const osqp_csc* P, const osqp_csc* A) {
   HostStructure h;
   build_host_structure(P, A, &h);
@@ -721,8 +883,19 @@ int32_t osqp_setup(osqp_solver** out, const osqp_csc* P, const double* q, const 
   {
     const long long nwarps =
         (long long)(s->use_grid ? s->grid : (s->use_cluster ? kClusterSize : 1)) * (kThreads / 32);
-    s->kn_s = make_sched(s->kn_rp, nwarps);
-    s->a_s = make_sched(s->a_rp, nwarps);
+    // grid team: time the candidate row partitions of both matrices on
+    // the device (settings->autotune) and keep the fastest
+    if (s->use_grid && settings->autotune) {
+      const bool f64 = settings->precision == OSQP_PRECISION_FP64;
+      s->tuned_kn =
+          f64 ? tune_grid_matrix<double>(s, true, s->kn_rp, s->kn_ci, n + m, nwarps, s->tune_kn_ms)
+              : tune_grid_matrix<float>(s, true, s->kn_rp, s->kn_ci, n + m, nwarps, s->tune_kn_ms);
+      s->tuned_a =
+          f64 ? tune_grid_matrix<double>(s, false, s->a_rp, s->a_ci, n, nwarps, s->tune_a_ms)
+              : tune_grid_matrix<float>(s, false, s->a_rp, s->a_ci, n, nwarps, s->tune_a_ms);
+    }
+    s->kn_s = make_sched(s->kn_rp, nwarps, std::max(s->tuned_kn, 0));
+    s->a_s = make_sched(s->a_rp, nwarps, std::max(s->tuned_a, 0));
     s->kn_ci = to_positions(s->kn_s, s->kn_ci, -1);
     s->kn_src = to_positions(s->kn_s, s->kn_src, -1);
     s->a_ci = to_positions(s->a_s, s->a_ci, -1);
@@ -957,6 +1130,20 @@ int32_t osqp_diag_scaling(osqp_solver* s, double* D, double* E, double* c, doubl
     CK(cudaMemcpyAsync(jacobi, gd, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
   if (c) CK(cudaMemcpyAsync(c, &s->sc->c, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
+  return OSQP_OK;
+}
+
+int32_t osqp_diag_schedule(osqp_solver* s, int32_t* groups, double* ms) {
+  if (!s || !groups) return OSQP_ERR_ARG;
+  groups[0] = s->kn_s.group;
+  groups[1] = s->a_s.group;
+  groups[2] = s->tuned_kn < 0 || s->tuned_a < 0 ? -1 : (s->tuned_kn > 0 || s->tuned_a > 0 ? 1 : 0);
+  if (ms) {
+    for (int k = 0; k < 6; ++k) {
+      ms[k] = s->tune_kn_ms[k];
+      ms[6 + k] = s->tune_a_ms[k];
+    }
+  }
   return OSQP_OK;
 }
 

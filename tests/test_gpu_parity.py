@@ -422,7 +422,9 @@ def test_long_rows_are_deterministic(launch, precision):
     qp = pb.config_problem(2)
     out = []
     for _ in range(2):
-        with Solver(qp, launch=launch, precision=precision, max_iter=200) as s:
+        # the rule's row partition (autotune = 0): a timed choice could give
+        # the two setups different partitions and so different rounding
+        with Solver(qp, launch=launch, precision=precision, max_iter=200, autotune=0) as s:
             g = s.solve()
         out.append(g)
     a, b = out
