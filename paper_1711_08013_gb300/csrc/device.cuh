@@ -33,7 +33,7 @@ constexpr int kMaxSumSlots = 4; // sum slots staged through shared memory per re
 // Shared memory of every team kernel: reduction partials and results
 // (34·kMaxRed), the sum-slot staging area, and the scalars of the PCG
 // recurrence that one warp updates for the whole CTA (kScalSlots).
-constexpr int kScalSlots = 8;
+constexpr int kScalSlots = 10;
 constexpr int kScalOff = 34 * kMaxRed + kMaxSumSlots * kThreads;
 constexpr int kSmemDoubles = kScalOff + kScalSlots;
 constexpr int kChunk = 256;     // nonzeros per long-row chunk
@@ -356,6 +356,13 @@ struct GridTeam {
     return *flag != 0;
   }
 
+  // publish, then a team barrier
+  template <int K, unsigned MAXMASK, typename V>
+  __device__ bool publish_sync(const V (&v)[K]) {
+    publish<K, MAXMASK>(v);
+    return sync();
+  }
+
   template <int K, unsigned MAXMASK, typename V>
   __device__ void publish(const V (&v)[K]) {
     block_reduce<K, MAXMASK>(v, sm);
@@ -488,6 +495,13 @@ struct ClusterTeam {
     return *flag != 0;
   }
 
+  // publish, then a team barrier
+  template <int K, unsigned MAXMASK, typename V>
+  __device__ bool publish_sync(const V (&v)[K]) {
+    publish<K, MAXMASK>(v);
+    return sync();
+  }
+
   template <int K, unsigned MAXMASK, typename V>
   __device__ void publish(const V (&v)[K]) {
     block_reduce<K, MAXMASK>(v, sm);
@@ -540,6 +554,13 @@ struct BlockTeam {
   template <int K, unsigned MAXMASK, typename V>
   __device__ void publish(const V (&v)[K]) {
     block_reduce<K, MAXMASK>(v, sm);
+  }
+  // publish, then a team barrier: block_reduce already ends with a CTA
+  // barrier, which orders every write made before it
+  template <int K, unsigned MAXMASK, typename V>
+  __device__ bool publish_sync(const V (&v)[K]) {
+    block_reduce<K, MAXMASK>(v, sm);
+    return true;
   }
   template <int K, unsigned MAXMASK>
   __device__ void collect(double (&out)[K]) {
@@ -729,13 +750,18 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sched& S, const int* 
   }
 }
 
-// Sum of long row lr's partial value v in chunk order, by one thread, after
-// the LAZY product that stored them (a team barrier in between).
+// Sum of long row lr's partial value v after the LAZY product that stored
+// them (a team barrier in between), by one warp: lane k adds chunks k, k+32,
+// … in order, then a fixed xor-shuffle tree, so every lane holds the same
+// total.  All lanes of the warp call it.
 template <typename AT>
-__device__ __forceinline__ AT long_sum(const Sched& S, int lr, int v) {
+__device__ __forceinline__ AT warp_long_sum(const Sched& S, int lr, int v) {
+  const int lane = threadIdx.x & 31;
   const int2 r = S.lrange[lr];
   AT acc = AT(0);
-  for (int k = 0; k < r.y; ++k) acc += (AT)__ldcg(S.cpart + (size_t)(r.x + k) * kMaxNV + v);
+  for (int k = lane; k < r.y; k += 32) acc += (AT)__ldcg(S.cpart + (size_t)(r.x + k) * kMaxNV + v);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
   return acc;
 }
 
@@ -869,8 +895,7 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
       d.E[i] *= dl;
       dev[0] = fmax(dev[0], fabs(1.0 - dl));
     }
-    tm.template publish<1, 1u>(dev);
-    if (!tm.sync()) return false;
+    if (!tm.template publish_sync<1, 1u>(dev)) return false;
     tm.template collect<1, 1u>(dev);
     ++passes;
     // Cost scaling γ = 1/max{mean_j ‖P̄_:,j‖∞, ‖q̄‖∞} with the new D.
@@ -882,16 +907,14 @@ __device__ bool scale_stage(Team& tm, const Dev<T>& d, const Params& P, double r
         [&](int j, double* acc) { d.nrm_n[j] = cc * d.D[j] * acc[0]; });
     double qn[1] = {0.0};
     for (int j = tid; j < n; j += nth) qn[0] = fmax(qn[0], fabs(cc * d.D[j] * d.q_raw[j]));
-    tm.template publish<1, 1u>(qn);
-    if (!tm.sync()) return false;
+    if (!tm.template publish_sync<1, 1u>(qn)) return false;
     tm.template collect<1, 1u>(qn);
     double sum[1] = {0.0};
     for (int j = tid; j < n; j += nth) {
       sum[0] += d.nrm_n[j];
       d.nrm_n[j] = 0.0;
     }
-    tm.template publish<1, 0u>(sum);
-    if (!tm.sync()) return false;
+    if (!tm.template publish_sync<1, 0u>(sum)) return false;
     tm.template collect<1, 0u>(sum);
     // In γ's max a norm below 1e-4 counts as 1 (a vanishing norm carries no
     // scale, as for δ), and the max is clamped like the other norms; taken
@@ -1105,8 +1128,7 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
       red[0] += r[j] * zj;
       red[1] = fmax(red[1], fabs(r[j]));
     }
-    tm.template publish<2, 2u>(red);
-    if (!tm.sync()) return false;
+    if (!tm.template publish_sync<2, 2u>(red)) return false;
     tm.template collect<2, 2u>(red);
     double rz = red[0];
     const double tol = kPolishPcgTol * red[1];
@@ -1131,8 +1153,7 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
           },
           [&](int j, double pv, double av) { kp[j] = pv + av + delta * p[j]; });
       for (int i = tid; i < m; i += nth) g[0] += delta * t[i] * t[i];
-      tm.template publish<1, 0u>(g);
-      if (!tm.sync()) return false;
+      if (!tm.template publish_sync<1, 0u>(g)) return false;
       tm.template collect<1, 0u>(g);
       if (!(g[0] > 0.0)) break;
       const double alpha_c = rz / g[0];
@@ -1146,8 +1167,7 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
         red2[0] += rj * zj;
         red2[1] = fmax(red2[1], fabs(rj));
       }
-      tm.template publish<2, 2u>(red2);
-      if (!tm.sync()) return false;
+      if (!tm.template publish_sync<2, 2u>(red2)) return false;
       tm.template collect<2, 2u>(red2);
       if (!(red2[1] > tol) || !(red2[0] > 0.0)) break;
       const double beta_c = red2[0] / rz;
@@ -1186,8 +1206,7 @@ __device__ __noinline__ bool polish_stage(Team& tm, const Dev<T>& d, const Param
       chk[2] = 1.0;
   }
   for (int j = tid; j < n; j += nth) chk[1] = fmax(chk[1], fabs((kp[j] + d.q[j]) / D[j]));
-  tm.template publish<4, 7u>(chk);
-  if (!tm.sync()) return false;
+  if (!tm.template publish_sync<4, 7u>(chk)) return false;
   tm.template collect<4, 7u>(chk);
   const double pr = chk[0], dr = chk[1] / c;
   const bool accept = chk[2] == 0.0 && pr <= *pr_io && dr <= *dr_io;
@@ -1316,10 +1335,10 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   const double c = d.sc->c;
   double rho_bar = d.sc->rho_bar;
   // Scalars of the PCG recurrence (γ, α, β, tolerance, and α, β and the stop
-  // flag handed to every thread), updated by warp 0 of each CTA after each
-  // reduction: every CTA derives the same values from the same reduced
-  // inputs, and the narrow FP64 pipe runs the divisions once per CTA rather
-  // than once per warp.
+  // flag handed to every thread; 1/γ and 1/α in slots 8 and 9), updated by
+  // warp 0 of each CTA after each reduction: every CTA derives the same
+  // values from the same reduced inputs, and the narrow FP64 pipe runs the
+  // divisions once per CTA rather than once per warp.
   double* scal = tm.sm + kScalOff;
   T* scalT = reinterpret_cast<T*>(scal + 5);
   int* sflag = reinterpret_cast<int*>(scal + 7);
@@ -1392,8 +1411,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
     double res[2] = {0.0, 0.0};
     for (int i = tid; i < m; i += nth) res[0] = fmax(res[0], fabs(d.ax[i] - z[i]));
     for (int j = tid; j < n; j += nth) res[1] = fmax(res[1], fabs(d.px[j] + d.q[j] + d.aty[j]));
-    tm.template publish<2, 3u>(res);
-    if (!tm.sync()) return false;
+    if (!tm.template publish_sync<2, 3u>(res)) return false;
     tm.template collect<2, 3u>(res);
     rp_bar = res[0];
     rd_bar = res[1];
@@ -1456,8 +1474,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           [&](int col, T v, T* acc) { acc[0] += v * (r[col] * dinv[col]); },
           [&](int i, T* acc) { t[i] = rhoT[i] * acc[0]; });
     }
-    tm.template publish<3, 6u>(red3t);
-    if (!tm.sync()) return false;
+    if (!tm.template publish_sync<3, 6u>(red3t)) return false;
     tm.template collect<3, 6u>(red3);
     if (warp0) {
       // PCG accuracy (reading of "up to some predefined accuracy", §3.1).
@@ -1491,12 +1508,14 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           },
           NoLong{}, LazyTag{});
       const T red1t[1] = {wacc};
-      tm.template publish<1, 0u>(red1t);
-      if (!tm.sync()) return false;
+      if (!tm.template publish_sync<1, 0u>(red1t)) return false;
       tm.template collect<1, 0u>(red1);
       if (warp0) {
         const double a = red1[0] > 0.0 ? scal[0] / red1[0] : 0.0;
+        const double inv_gamma = 1.0 / scal[0];
         scal[1] = a;
+        scal[8] = inv_gamma;
+        scal[9] = red1[0] * inv_gamma;  // 1/α
         scalT[0] = T(a);
         scalT[1] = T(0);
         if (threadIdx.x == 0) *sflag = !(red1[0] > 0.0);
@@ -1520,11 +1539,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         const T* __restrict__ tc = ubuf(cur) + n;
         const T* __restrict__ u = ubuf(cur);
         T* __restrict__ un = ubuf(nxt);
-        const bool lazy_w = d.kn.nlong > 0;
-        for (int j = tid; j < n; j += nth) {
-          T wj;  // w = Ku, its long rows summed here from the product's partials
-          if (lazy_w && d.kn.lidx[j] >= 0) wj = sigT * u[j] + long_sum<T>(d.kn, d.kn.lidx[j], 0);
-          else wj = wc[j];
+        auto upd = [&](int j, T wj) {
           const T pj = first ? u[j] : u[j] + bT * pv[j];
           const T sj = first ? wj : wj + bT * sc[j];
           pv[j] = pj;
@@ -1533,6 +1548,16 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           const T rj = rc[j] - aT * sj;
           rn[j] = rj;
           un[j] = rj * dinv[j];
+        };
+        // w = Ku; its long rows are left as the product's chunk partials and
+        // summed here, one warp per row
+        const bool lazy_w = d.kn.nlong > 0;
+        for (int j = tid; j < n; j += nth)
+          if (!lazy_w || d.kn.lidx[j] < 0) upd(j, wc[j]);
+        for (int lr = tm.warp(); lr < d.kn.nlong; lr += tm.nwarps()) {
+          const T sum = warp_long_sum<T>(d.kn, lr, 0);
+          const int j = d.kn.long_rows[lr];
+          if ((threadIdx.x & 31) == 0) upd(j, sigT * u[j] + sum);
         }
         for (int i = tid; i < m; i += nth) {
           const T ti = rho_invT[i] * tc[i];
@@ -1582,8 +1607,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         red2t[1] = g1;
         red2t[2] = g2;
       }
-      tm.template publish<3, 4u>(red2t);
-      if (!tm.sync()) return false;
+      if (!tm.template publish_sync<3, 4u>(red2t)) return false;
       tm.template collect<3, 4u>(red2);
       cur = nxt;
       if (warp0) {
@@ -1592,8 +1616,11 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         int stop = !(red2[2] > scal[3]) || j_it >= P.pcg_max_iter;
         if (!stop) {
           const double gamma_n = red2[0];
-          const double beta_n = gamma_n / scal[0];
-          const double denom = red2[1] - beta_n * gamma_n / scal[1];
+          // 1/γ' for the next update runs beside this one's chain, which
+          // keeps a single division: β = γ'·(1/γ), γ'/α = γ'·(1/α)
+          const double inv_gamma_n = 1.0 / gamma_n;
+          const double beta_n = gamma_n * scal[8];
+          const double denom = red2[1] - beta_n * (gamma_n * scal[9]);
           if (!(denom > 0.0) || !(gamma_n > 0.0)) {
             stop = 1;
           } else {
@@ -1601,6 +1628,8 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
             scal[0] = gamma_n;
             scal[1] = a;
             scal[2] = beta_n;
+            scal[8] = inv_gamma_n;
+            scal[9] = denom * inv_gamma_n;  // 1/α
             scalT[0] = T(a);
             scalT[1] = T(beta_n);
           }
@@ -1731,8 +1760,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
       R[22] += qj * x[j];
     }
     if (threadIdx.x == 0) R[23] = (double)(gtimer() - t_start);
-    tm.template publish<24, kMaxMask>(R);
-    if (!tm.sync()) return false;
+    if (!tm.template publish_sync<24, kMaxMask>(R)) return false;
     tm.template collect<24, kMaxMask>(R);
     prim_res = R[0];
     dual_res = R[6] / c;
