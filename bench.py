@@ -486,6 +486,17 @@ def batch_main(args, ws, rank, local):
     e2e_dt = D.max_over_ranks(time.perf_counter() - t0, device=dev)
     traffic = (TRAFFIC_BATCH_PER_PROBLEM[args.precision] * local_count
                if args.precision in TRAFFIC_BATCH_PER_PROBLEM else None)
+    # the row partitions in use: per shape class the autotuner's measured
+    # choice (or the rule's, autotune = 0), counted over this rank's problems
+    table = B.osqp_batch_tuning(h)
+    chosen = {}
+    for i in range(local_count):
+        g = B.osqp_batch_schedule(h, i)
+        for kind, name in ((0, "Kn"), (1, "A")):
+            key = f"{name}:G{g[kind]}"
+            chosen[key] = chosen.get(key, 0) + 1
+    row_partition = {"chosen_by": "timing" if table else "rule", "shape_classes": len(table),
+                     "problems_per_width": dict(sorted(chosen.items()))}
     line = {
         "metric": METRIC, "value": solves_all / total_max, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps,
@@ -495,7 +506,8 @@ def batch_main(args, ws, rank, local):
                    "precision": args.precision, "eps": 1e-3,
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": (f"one set of {count * ws} problems sharded over {ws} GPUs "
-                                   "(LPT on estimated work)") if ws > 1 else "single"},
+                                   "(LPT on estimated work)") if ws > 1 else "single",
+                   "row_partition": row_partition},
         "admm_iter_per_s": iters_all / (total_max / args.steps),
         "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[int(0.99 * (len(lat) - 1))],
         "admm_iters_per_solve": iters / local_count,
