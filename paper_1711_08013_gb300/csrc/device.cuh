@@ -1335,10 +1335,10 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   const double c = d.sc->c;
   double rho_bar = d.sc->rho_bar;
   // Scalars of the PCG recurrence (γ, α, β, tolerance, and α, β and the stop
-  // flag handed to every thread; 1/γ and 1/α in slots 8 and 9), updated by
-  // warp 0 of each CTA after each reduction: every CTA derives the same
-  // values from the same reduced inputs, and the narrow FP64 pipe runs the
-  // divisions once per CTA rather than once per warp.
+  // flag handed to every thread; in FP32-mixed mode 1/γ and 1/α in slots 8
+  // and 9), updated by warp 0 of each CTA after each reduction: every CTA
+  // derives the same values from the same reduced inputs, and the narrow
+  // FP64 pipe runs the divisions once per CTA rather than once per warp.
   double* scal = tm.sm + kScalOff;
   T* scalT = reinterpret_cast<T*>(scal + 5);
   int* sflag = reinterpret_cast<int*>(scal + 7);
@@ -1550,11 +1550,13 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           un[j] = rj * dinv[j];
         };
         // w = Ku; its long rows are left as the product's chunk partials and
-        // summed here, one warp per row
+        // summed here, one warp per row, taken from the last warp down: the
+        // elements above go to the first threads, so on a wide team the two
+        // chains run on different warps
         const bool lazy_w = d.kn.nlong > 0;
         for (int j = tid; j < n; j += nth)
           if (!lazy_w || d.kn.lidx[j] < 0) upd(j, wc[j]);
-        for (int lr = tm.warp(); lr < d.kn.nlong; lr += tm.nwarps()) {
+        for (int lr = tm.nwarps() - 1 - tm.warp(); lr < d.kn.nlong; lr += tm.nwarps()) {
           const T sum = warp_long_sum<T>(d.kn, lr, 0);
           const int j = d.kn.long_rows[lr];
           if ((threadIdx.x & 31) == 0) upd(j, sigT * u[j] + sum);
@@ -1616,11 +1618,20 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         int stop = !(red2[2] > scal[3]) || j_it >= P.pcg_max_iter;
         if (!stop) {
           const double gamma_n = red2[0];
-          // 1/γ' for the next update runs beside this one's chain, which
-          // keeps a single division: β = γ'·(1/γ), γ'/α = γ'·(1/α)
-          const double inv_gamma_n = 1.0 / gamma_n;
-          const double beta_n = gamma_n * scal[8];
-          const double denom = red2[1] - beta_n * (gamma_n * scal[9]);
+          // β = γ'/γ and γ'/α.  FP32-mixed: from the reciprocals kept from
+          // the previous update (1/γ' runs beside this chain), so a single
+          // division is left on it.  FP64: the two quotients, independent
+          // of each other, correctly rounded (the FP64 PCG iteration count
+          // follows the rounding of these scalars).
+          double beta_n, denom, inv_gamma_n = 0.0;
+          if constexpr (sizeof(T) == sizeof(float)) {
+            inv_gamma_n = 1.0 / gamma_n;
+            beta_n = gamma_n * scal[8];
+            denom = red2[1] - beta_n * (gamma_n * scal[9]);
+          } else {
+            beta_n = gamma_n / scal[0];
+            denom = red2[1] - beta_n * (gamma_n / scal[1]);
+          }
           if (!(denom > 0.0) || !(gamma_n > 0.0)) {
             stop = 1;
           } else {
@@ -1628,8 +1639,10 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
             scal[0] = gamma_n;
             scal[1] = a;
             scal[2] = beta_n;
-            scal[8] = inv_gamma_n;
-            scal[9] = denom * inv_gamma_n;  // 1/α
+            if constexpr (sizeof(T) == sizeof(float)) {
+              scal[8] = inv_gamma_n;
+              scal[9] = denom * inv_gamma_n;  // 1/α
+            }
             scalT[0] = T(a);
             scalT[1] = T(beta_n);
           }
