@@ -65,9 +65,9 @@ PARAM_LEN = {"lasso_path": 100, "mpc_loop": 100, "portfolio_bt": 960}
 # problems scaled by the problems of the launch.  Absent: not captured
 # since the kernels last changed.  The single-problem figure holds for the
 # row partitions it was captured with (group widths of Kn and Ā).
-TRAFFIC = {("lasso", "fp64"): 19.733248e6}
+TRAFFIC = {("lasso", "fp64"): 20.403456e6}
 TRAFFIC_GROUPS = {("lasso", "fp64"): (2, 2)}
-TRAFFIC_BATCH_PER_PROBLEM = {"fp32": 4.004333e9 / 608}
+TRAFFIC_BATCH_PER_PROBLEM = {"fp32": 3.380327168e9 / 608}
 # Mean time per QP and mean iterations per QP that the paper reports for the
 # same sequences (OSQP direct method on a CPU; context only)
 PARAM_PAPER = {

@@ -32,8 +32,14 @@ constexpr int kMaxRed = 32;     // reduction slots
 constexpr int kMaxSumSlots = 4; // sum slots staged through shared memory per reduction
 // Shared memory of every team kernel: reduction partials and results
 // (34·kMaxRed), the sum-slot staging area, and the scalars of the PCG
-// recurrence that one warp updates for the whole CTA (kScalSlots).
-constexpr int kScalSlots = 10;
+// recurrence that one warp updates for the whole CTA (kScalSlots).  In the
+// FP32-mixed mode five more slots hold the results of the last
+// working-precision reduction as unevaluated sums of two floats (kScalMirror,
+// one (high, low) pair per result, four results) and the PCG tolerance
+// (kScalTolF), from which every thread runs the CG scalar recurrence itself.
+constexpr int kScalMirror = 8;
+constexpr int kScalTolF = 12;
+constexpr int kScalSlots = 13;
 constexpr int kScalOff = 34 * kMaxRed + kMaxSumSlots * kThreads;
 constexpr int kSmemDoubles = kScalOff + kScalSlots;
 constexpr int kChunk = 256;     // nonzeros per long-row chunk
@@ -242,6 +248,67 @@ __device__ __forceinline__ float funkey(unsigned k) {
   return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
 }
 
+// Double-float arithmetic: a value held as the unevaluated sum h + l of two
+// floats with |l| ≤ ulp(h)/2, about 48 significant bits from FP32
+// instructions alone.  The error-free transformations are Knuth's TwoSum,
+// Dekker's FastTwoSum and the product error taken exactly by one fused
+// multiply-add; every operation is an explicitly rounded intrinsic, so the
+// compiler neither contracts nor reorders them.
+struct ff {
+  float h, l;
+};
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {  // |a| ≥ |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// x − y; the closing TwoSum keeps the low part when the high parts cancel
+__device__ __forceinline__ ff ff_sub(ff x, ff y) {
+  const ff s = ff_two_sum(x.h, -y.h);
+  return ff_two_sum(s.h, __fadd_rn(s.l, __fsub_rn(x.l, y.l)));
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  return ff_fast_two_sum(p, e);
+}
+// x / y: the FP32 quotient, then one correction from the remainder x − q·y
+__device__ __forceinline__ ff ff_div(ff x, ff y) {
+  const float q = __fdiv_rn(x.h, y.h);
+  const ff r = ff_sub(x, ff_mul(y, ff{q, 0.0f}));
+  return ff_fast_two_sum(q, __fdiv_rn(r.h, y.h));
+}
+// the pair nearest to a double
+__device__ __forceinline__ ff ff_of(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+// result k of the last reduction as a double-float pair at kScalMirror
+__device__ __forceinline__ void mirror_store(double* sm, int k, ff v) {
+  float* m = reinterpret_cast<float*>(sm + kScalOff + kScalMirror);
+  m[2 * k] = v.h;
+  m[2 * k + 1] = v.l;
+}
+
+// One level of a warp's shuffle tree over (sum, error) pairs of FP32 terms:
+// the partner's pair is added by Knuth's TwoSum, whose rounding error joins
+// the error term.
+__device__ __forceinline__ void two_sum_level(float& hi, float& lo, int off) {
+  const float b = __shfl_xor_sync(0xffffffffu, hi, off);
+  const float bl = __shfl_xor_sync(0xffffffffu, lo, off);
+  const float s = __fadd_rn(hi, b);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(bl, err));
+}
+
 // Block-wide reduction of K working-precision (FP32) slots with the result
 // in FP64, for the FP32-mixed mode: each warp sums its lanes' values by a
 // shuffle tree of error-free FP32 additions (Knuth's TwoSum, the rounding
@@ -249,12 +316,17 @@ __device__ __forceinline__ float funkey(unsigned k) {
 // one warp per slot then converts the warps' pairs to FP64 and adds them,
 // so the narrow FP64 pipe sees one instruction per slot rather than one per
 // warp.  Max slots combine order-preserving keys.  Result in
-// sm[32*kMaxRed + k], as block_reduce.  All threads call it.
-template <int K, unsigned MAXMASK>
+// sm[32*kMaxRed + k], as block_reduce, and as a double-float pair at
+// kScalMirror.
+// With DBL false only the double-float result is formed, without FP64
+// instructions: the warps' pairs are combined by the same TwoSum tree.  All
+// threads call it.
+template <int K, unsigned MAXMASK, bool DBL = true>
 __device__ __forceinline__ void block_reduce(const float (&v)[K], double* sm) {
   static_assert(K <= kMaxSumSlots, "too many slots");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   float2* pw = reinterpret_cast<float2*>(sm);  // [warp · kMaxRed + slot]
+  float* mirror = reinterpret_cast<float*>(sm + kScalOff + kScalMirror);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if ((MAXMASK >> k) & 1u) {
@@ -268,15 +340,7 @@ __device__ __forceinline__ void block_reduce(const float (&v)[K], double* sm) {
     } else {
       float hi = v[k], lo = 0.0f;
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float b = __shfl_xor_sync(0xffffffffu, hi, off);
-        const float bl = __shfl_xor_sync(0xffffffffu, lo, off);
-        const float s = __fadd_rn(hi, b);
-        const float bb = __fsub_rn(s, hi);
-        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-        hi = s;
-        lo = __fadd_rn(lo, __fadd_rn(bl, err));
-      }
+      for (int off = 16; off > 0; off >>= 1) two_sum_level(hi, lo, off);
       if (lane == 0) pw[wid * kMaxRed + k] = make_float2(hi, lo);
     }
   }
@@ -286,15 +350,38 @@ __device__ __forceinline__ void block_reduce(const float (&v)[K], double* sm) {
     const bool mx = (MAXMASK >> k) & 1u;
     const float2 e = lane < nw ? pw[lane * kMaxRed + k] : make_float2(mx ? -INFINITY : 0.0f, 0.0f);
     if (mx) {
-      unsigned long long x = dkey((double)e.x);
+      unsigned x = fkey(e.x);
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) x = umax64(x, __shfl_xor_sync(0xffffffffu, x, off));
-      if (lane == 0) sm[32 * kMaxRed + k] = dunkey(x);
-    } else {
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned o = __shfl_xor_sync(0xffffffffu, x, off);
+        x = x > o ? x : o;
+      }
+      if (lane == 0) {
+        const float f = funkey(x);
+        if (DBL) sm[32 * kMaxRed + k] = (double)f;
+        mirror[2 * k] = f;
+        mirror[2 * k + 1] = 0.0f;
+      }
+    } else if (DBL) {
       double x = (double)e.x + (double)e.y;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-      if (lane == 0) sm[32 * kMaxRed + k] = x;
+      if (lane == 0) {
+        sm[32 * kMaxRed + k] = x;
+        const ff f = ff_of(x);
+        mirror[2 * k] = f.h;
+        mirror[2 * k + 1] = f.l;
+      }
+    } else {
+      // FP32 result only: the warps' pairs combined by the same TwoSum tree
+      float hi = e.x, lo = e.y;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) two_sum_level(hi, lo, off);
+      if (lane == 0) {
+        const ff f = ff_two_sum(hi, lo);
+        mirror[2 * k] = f.h;
+        mirror[2 * k + 1] = f.l;
+      }
     }
   }
   __syncthreads();
@@ -356,8 +443,9 @@ struct GridTeam {
     return *flag != 0;
   }
 
-  // publish, then a team barrier
-  template <int K, unsigned MAXMASK, typename V>
+  // publish, then a team barrier (DBL is ignored: the CTAs' partials are
+  // combined in FP64)
+  template <int K, unsigned MAXMASK, bool DBL = true, typename V>
   __device__ bool publish_sync(const V (&v)[K]) {
     publish<K, MAXMASK>(v);
     return sync();
@@ -374,8 +462,10 @@ struct GridTeam {
   // Combine the partials of the last publish (after a sync).  Every CTA runs
   // the same fixed-order combination, so all threads see identical values.
   // Each lane issues all of its (≤ 16) partial loads before combining them.
-  template <int K, unsigned MAXMASK>
+  // MIRROR: also leave the results as double-float pairs at kScalMirror.
+  template <int K, unsigned MAXMASK, bool MIRROR = false>
   __device__ void collect(double (&out)[K]) {
+    static_assert(!MIRROR || K <= 4, "four mirrored results at most");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nb = gridDim.x;
     for (int k = wid; k < K; k += nw) {
@@ -397,7 +487,10 @@ struct GridTeam {
           if (u < per) x = umax64(x, dkey(y[u]));
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x = umax64(x, __shfl_xor_sync(0xffffffffu, x, off));
-        if (lane == 0) sm[33 * kMaxRed + k] = dunkey(x);
+        if (lane == 0) {
+          sm[33 * kMaxRed + k] = dunkey(x);
+          if (MIRROR) mirror_store(sm, k, ff{(float)dunkey(x), 0.0f});
+        }
       } else {
         double x = y[0];
 #pragma unroll
@@ -405,7 +498,10 @@ struct GridTeam {
           if (u < per) x += y[u];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-        if (lane == 0) sm[33 * kMaxRed + k] = x;
+        if (lane == 0) {
+          sm[33 * kMaxRed + k] = x;
+          if (MIRROR) mirror_store(sm, k, ff_of(x));
+        }
       }
     }
     __syncthreads();
@@ -495,8 +591,9 @@ struct ClusterTeam {
     return *flag != 0;
   }
 
-  // publish, then a team barrier
-  template <int K, unsigned MAXMASK, typename V>
+  // publish, then a team barrier (DBL is ignored: the CTAs' partials are
+  // combined in FP64)
+  template <int K, unsigned MAXMASK, bool DBL = true, typename V>
   __device__ bool publish_sync(const V (&v)[K]) {
     publish<K, MAXMASK>(v);
     return sync();
@@ -509,8 +606,10 @@ struct ClusterTeam {
   }
 
   // Combine the partials of the last publish (after a sync), in rank order.
-  template <int K, unsigned MAXMASK>
+  // MIRROR: also leave the results as double-float pairs at kScalMirror.
+  template <int K, unsigned MAXMASK, bool MIRROR = false>
   __device__ void collect(double (&out)[K]) {
+    static_assert(!MIRROR || K <= 4, "four mirrored results at most");
     if (threadIdx.x < K) {
       const int k = threadIdx.x;
       const bool mx = (MAXMASK >> k) & 1u;
@@ -524,12 +623,14 @@ struct ClusterTeam {
         for (int r = 1; r < 16; ++r)
           if (r < (int)csize) x = umax64(x, dkey(y[r]));
         sm[33 * kMaxRed + k] = dunkey(x);
+        if (MIRROR) mirror_store(sm, k, ff{(float)dunkey(x), 0.0f});
       } else {
         double x = y[0];
 #pragma unroll
         for (int r = 1; r < 16; ++r)
           if (r < (int)csize) x += y[r];
         sm[33 * kMaxRed + k] = x;
+        if (MIRROR) mirror_store(sm, k, ff_of(x));
       }
     }
     __syncthreads();
@@ -556,13 +657,19 @@ struct BlockTeam {
     block_reduce<K, MAXMASK>(v, sm);
   }
   // publish, then a team barrier: block_reduce already ends with a CTA
-  // barrier, which orders every write made before it
-  template <int K, unsigned MAXMASK, typename V>
+  // barrier, which orders every write made before it.  DBL false (FP32
+  // values only): the caller reads only the double-float results at
+  // kScalMirror.
+  template <int K, unsigned MAXMASK, bool DBL = true, typename V>
   __device__ bool publish_sync(const V (&v)[K]) {
-    block_reduce<K, MAXMASK>(v, sm);
+    if constexpr (sizeof(V) == sizeof(float))
+      block_reduce<K, MAXMASK, DBL>(v, sm);
+    else
+      block_reduce<K, MAXMASK>(v, sm);
     return true;
   }
-  template <int K, unsigned MAXMASK>
+  // the FP32 copies (MIRROR) are left by the FP32 block_reduce itself
+  template <int K, unsigned MAXMASK, bool MIRROR = false>
   __device__ void collect(double (&out)[K]) {
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = sm[32 * kMaxRed + k];
@@ -1334,15 +1441,31 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
   const T sigT = T(sigma);
   const double c = d.sc->c;
   double rho_bar = d.sc->rho_bar;
-  // Scalars of the PCG recurrence (γ, α, β, tolerance, and α, β and the stop
-  // flag handed to every thread; in FP32-mixed mode 1/γ and 1/α in slots 8
-  // and 9), updated by warp 0 of each CTA after each reduction: every CTA
-  // derives the same values from the same reduced inputs, and the narrow
-  // FP64 pipe runs the divisions once per CTA rather than once per warp.
+  // FP64 mode: scalars of the PCG recurrence (γ, α, β, tolerance, and α, β
+  // and the stop flag handed to every thread), updated by warp 0 of each CTA
+  // after each reduction: every CTA derives the same values from the same
+  // reduced inputs, and the narrow FP64 pipe runs the divisions once per CTA
+  // rather than once per warp.
   double* scal = tm.sm + kScalOff;
   T* scalT = reinterpret_cast<T*>(scal + 5);
   int* sflag = reinterpret_cast<int*>(scal + 7);
   const bool warp0 = (threadIdx.x >> 5) == 0;
+  // FP32-mixed mode: every thread runs the recurrence itself, in
+  // double-float arithmetic on FP32 instructions, from the reduced values
+  // that the reduction leaves as double-float pairs (identical inputs and
+  // operations in every thread give identical scalars), and keeps 1/γ and
+  // 1/α as pairs and α, β as floats in registers: no FP64 instruction and
+  // no CTA barrier after the reduction.  The pairs keep the accuracy of the
+  // FP64 reduction of the FP32 partial sums, which the denominator
+  // (w,u) − β·γ'/α needs: it cancels when CG converges slowly, and with
+  // both terms rounded to FP32 the ADMM iteration of the portfolio problem
+  // at ε = 1e-7 diverged.
+  constexpr bool kF32 = sizeof(T) == sizeof(float);
+  const float* fmir = reinterpret_cast<const float*>(scal + kScalMirror);
+  float* ftol = reinterpret_cast<float*>(scal + kScalTolF);
+  ff cg_g{0.0f, 0.0f}, cg_ig{0.0f, 0.0f}, cg_ia{0.0f, 0.0f};
+  float cg_tol = 0.0f;
+  T cg_a = T(0), cg_b = T(0);
   const unsigned long long t_start = gtimer();
   // Pointers read once (restrict-qualified for the compiler).
   const int* __restrict__ kn_ci = d.kn_ci;
@@ -1475,7 +1598,7 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           [&](int i, T* acc) { t[i] = rhoT[i] * acc[0]; });
     }
     if (!tm.template publish_sync<3, 6u>(red3t)) return false;
-    tm.template collect<3, 6u>(red3);
+    tm.template collect<3, 6u, kF32>(red3);
     if (warp0) {
       // PCG accuracy (reading of "up to some predefined accuracy", §3.1).
       const double bnorm = red3[2];
@@ -1484,10 +1607,15 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
                                          : 0.1 * P.pcg_kappa * bnorm);
       scal[0] = red3[0];  // γ = (r, M⁻¹r)
       scal[3] = tol;
+      if (kF32 && threadIdx.x == 0) *ftol = (float)tol;
       if (threadIdx.x == 0) *sflag = !(red3[1] > tol);
     }
     __syncthreads();
     bool done = *sflag != 0;
+    if constexpr (kF32) {
+      cg_g = ff{fmir[0], fmir[1]};
+      cg_tol = *ftol;
+    }
     if (!done) {
       // --- W: w = Ku, (w,u)
       double red1[1] = {0.0};
@@ -1508,26 +1636,35 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
           },
           NoLong{}, LazyTag{});
       const T red1t[1] = {wacc};
-      if (!tm.template publish_sync<1, 0u>(red1t)) return false;
-      tm.template collect<1, 0u>(red1);
-      if (warp0) {
-        const double a = red1[0] > 0.0 ? scal[0] / red1[0] : 0.0;
-        const double inv_gamma = 1.0 / scal[0];
-        scal[1] = a;
-        scal[8] = inv_gamma;
-        scal[9] = red1[0] * inv_gamma;  // 1/α
-        scalT[0] = T(a);
-        scalT[1] = T(0);
-        if (threadIdx.x == 0) *sflag = !(red1[0] > 0.0);
+      if (!tm.template publish_sync<1, 0u, !kF32>(red1t)) return false;
+      tm.template collect<1, 0u, kF32>(red1);
+      if constexpr (kF32) {
+        // α = γ/(w,u), β = 0; every thread, from the pair of (w,u)
+        const ff wu{fmir[0], fmir[1]};
+        done = !(wu.h > 0.0f);
+        if (!done) {
+          cg_a = ff_div(cg_g, wu).h;
+          cg_b = 0.0f;
+          cg_ig = ff_div(ff{1.0f, 0.0f}, cg_g);
+          cg_ia = ff_mul(wu, cg_ig);  // 1/α
+        }
+      } else {
+        if (warp0) {
+          const double a = red1[0] > 0.0 ? scal[0] / red1[0] : 0.0;
+          scal[1] = a;
+          scalT[0] = T(a);
+          scalT[1] = T(0);
+          if (threadIdx.x == 0) *sflag = !(red1[0] > 0.0);
+        }
+        __syncthreads();
+        done = *sflag != 0;
       }
-      __syncthreads();
-      done = *sflag != 0;
     }
     int j_it = 0;
     while (!done) {
       const int nxt = cur ^ 1;
       const bool first = j_it == 0;
-      const T aT = scalT[0], bT = scalT[1];
+      const T aT = kF32 ? cg_a : scalT[0], bT = kF32 ? cg_b : scalT[1];
       // --- P1: p = u + βp, s = w + βs, x̃ += αp, r −= αs, u = M⁻¹r,
       //         Āp = t/ρ + β·Āp, z̃ += α·Āp   (elementwise)
       {
@@ -1609,29 +1746,41 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
         red2t[1] = g1;
         red2t[2] = g2;
       }
-      if (!tm.template publish_sync<3, 4u>(red2t)) return false;
-      tm.template collect<3, 4u>(red2);
+      if (!tm.template publish_sync<3, 4u, !kF32>(red2t)) return false;
+      tm.template collect<3, 4u, kF32>(red2);
       cur = nxt;
+      if constexpr (kF32) {
+        // Chronopoulos–Gear update in every thread, in double-float (see
+        // above): β = γ'·(1/γ), α = γ'/((w,u) − β·γ'·(1/α)); stop at the
+        // tolerance, the iteration cap, or a breakdown
+        bool stop = !(fmir[4] > cg_tol) || j_it >= P.pcg_max_iter;
+        if (!stop) {
+          const ff gn{fmir[0], fmir[1]};
+          const ff beta = ff_mul(gn, cg_ig);
+          const ff denom = ff_sub(ff{fmir[2], fmir[3]}, ff_mul(beta, ff_mul(gn, cg_ia)));
+          if (!(denom.h > 0.0f) || !(gn.h > 0.0f)) {
+            stop = true;
+          } else {
+            cg_a = ff_div(gn, denom).h;
+            cg_b = beta.h;
+            cg_ig = ff_div(ff{1.0f, 0.0f}, gn);
+            cg_ia = ff_mul(denom, cg_ig);
+          }
+        }
+        if (stop) break;
+        continue;
+      }
       if (warp0) {
         // Chronopoulos–Gear update: β = γ'/γ, α = γ'/((w,u) − βγ'/α); stop
-        // at the tolerance, the iteration cap, or a breakdown (p vanished)
+        // at the tolerance, the iteration cap, or a breakdown (p vanished).
+        // β = γ'/γ and γ'/α are independent of each other and correctly
+        // rounded: the FP64 PCG iteration count follows the rounding of
+        // these scalars.
         int stop = !(red2[2] > scal[3]) || j_it >= P.pcg_max_iter;
         if (!stop) {
           const double gamma_n = red2[0];
-          // β = γ'/γ and γ'/α.  FP32-mixed: from the reciprocals kept from
-          // the previous update (1/γ' runs beside this chain), so a single
-          // division is left on it.  FP64: the two quotients, independent
-          // of each other, correctly rounded (the FP64 PCG iteration count
-          // follows the rounding of these scalars).
-          double beta_n, denom, inv_gamma_n = 0.0;
-          if constexpr (sizeof(T) == sizeof(float)) {
-            inv_gamma_n = 1.0 / gamma_n;
-            beta_n = gamma_n * scal[8];
-            denom = red2[1] - beta_n * (gamma_n * scal[9]);
-          } else {
-            beta_n = gamma_n / scal[0];
-            denom = red2[1] - beta_n * (gamma_n / scal[1]);
-          }
+          const double beta_n = gamma_n / scal[0];
+          const double denom = red2[1] - beta_n * (gamma_n / scal[1]);
           if (!(denom > 0.0) || !(gamma_n > 0.0)) {
             stop = 1;
           } else {
@@ -1639,10 +1788,6 @@ __device__ bool admm_stage(Team& tm, const Dev<T>& d, const Params& P) {
             scal[0] = gamma_n;
             scal[1] = a;
             scal[2] = beta_n;
-            if constexpr (sizeof(T) == sizeof(float)) {
-              scal[8] = inv_gamma_n;
-              scal[9] = denom * inv_gamma_n;  // 1/α
-            }
             scalT[0] = T(a);
             scalT[1] = T(beta_n);
           }

@@ -26,6 +26,25 @@ def acceptance(qp, x, y, eps_abs, eps_rel):
     return prim, dual, eps_p, eps_d
 
 
+U32 = 2.0 ** -24  # unit roundoff of IEEE single precision (round to nearest)
+
+
+def fp32_data_allowance(qp, x, y):
+    """How far the residuals of (x, y) can move when every entry of P and A
+    is rounded to FP32: each entry then carries a relative error of at most
+    2⁻²⁴, whatever diagonal scaling precedes the rounding, so the primal
+    residual moves by at most u·‖|A||x|‖∞ and the dual one by at most
+    u·‖|P||x| + |Aᵀ||y|‖∞.  A solver that keeps its matrices in FP32
+    certifies its tolerances on the rounded problem; on the problem as given
+    its residuals may exceed them by these amounts and no more."""
+    P = abs(full_P(qp))
+    A = abs(qp.A)
+    ax, ay = np.abs(x), np.abs(y)
+    ap = U32 * np.max(A @ ax, initial=0.0) if qp.m else 0.0
+    ad = U32 * np.max(P @ ax + A.T @ ay)
+    return float(ap), float(ad)
+
+
 def objective(qp, x):
     P = full_P(qp)
     return 0.5 * x @ (P @ x) + qp.q @ x
