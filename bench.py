@@ -46,7 +46,7 @@ WORKLOADS = {
                      "variables (x,y) n=10100, rows m=10101"),
     "mpc_batch": (3, "4096 ragged MPC QPs per GPU, nx~U{4..32}, nu=nx/2, T~U{10..30}, one "
                      "persistent launch (cold: scaling + ADMM per problem)"),
-    "serve": (4, "serving: Poisson arrivals at 2000 req/s over a pool of 256 random-QP (m=10n) and "
+    "serve": (4, "serving: Poisson arrivals at RATE req/s over a pool of 256 random-QP (m=10n) and "
                  "256 Huber (100n x n) problem IDs, n~logU[10,NMAX], warm-started perturbed q/l/u"),
     "svm": (None, "SVM QP (App. A.7): 100 features, 10000 points at 15% density, labels split in half; "
                   "variables (x,t) n=10100, rows m=20000"),
@@ -245,12 +245,18 @@ def param_oracle(name, k, budget_s=15.0):
     return done, time.perf_counter() - t0, iters
 
 
+def workload_desc(args, workload):
+    """The workload's description with its size and rate parameters filled in."""
+    return (WORKLOADS[workload][1].replace("NMAX", str(getattr(args, "nmax", "NMAX")))
+            .replace("RATE", f"{getattr(args, 'rate', 0):g}"))
+
+
 def _reference_line(args, workload, value, steps, dt, iters, sample, cores):
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
         "warmup": 0, "ms_per_step": 1e3 * dt / max(1, steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "impl": "reference", "config": {"workload": WORKLOADS[workload][1], "precision": "fp64",
+        "impl": "reference", "config": {"workload": workload_desc(args, workload), "precision": "fp64",
                                          "eps": 1e-3},
         "admm_iter_per_s": iters / dt if iters is not None else None,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -325,7 +331,7 @@ def run_reference(args, ws, rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": done,
             "warmup": 0, "ms_per_step": 1e3 * dt / done, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": {"workload": WORKLOADS[args.workload][1],
+            "impl": "reference", "config": {"workload": workload_desc(args, args.workload),
                                              "precision": "fp64", "eps": 1e-3},
             "admm_iter_per_s": iters / dt,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -691,7 +697,7 @@ def serve_main(args, ws, rank, local):
         "metric": METRIC, "value": total / wall, "unit": UNIT, "n_gpus": ws, "steps": 1,
         "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == B.FP64 else "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS["serve"][1].replace("NMAX", str(args.nmax)),
+        "config": {"workload": workload_desc(args, "serve"),
                    "offered_req_per_s": args.rate, "duration_s": args.duration,
                    "pool": len(spec), "slots": slots, "large_slots": large_slots,
                    "max_batch": None, "precision": args.precision, "eps": 1e-3,
