@@ -62,9 +62,13 @@ extern "C" {
 
 /* ---- precision modes ------------------------------------------------------ */
 #define OSQP_PRECISION_FP64 0       /* matrices, PCG and iterates in FP64 */
-#define OSQP_PRECISION_FP32_MIXED 1 /* scaled matrices and PCG vectors in FP32;
-                                       iterates, residual norms, termination,
-                                       ρ ratios and certificates in FP64 */
+#define OSQP_PRECISION_FP32_MIXED 1 /* scaled matrices and PCG vectors in FP32,
+                                       CG scalars in double-float on FP32
+                                       instructions; iterates, residual norms,
+                                       termination, ρ ratios and certificates
+                                       in FP64.  The tolerances are met on the
+                                       problem with its scaled matrices rounded
+                                       to FP32 */
 
 typedef struct {
   int32_t n_rows, n_cols, nnz;
