@@ -88,6 +88,9 @@ def parse():
                     help="default: fp32 (mixed) for mpc_batch, fp64 otherwise")
     ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
                     help="1: row partitions chosen by timing at setup; 0: the row-length rule")
+    ap.add_argument("--launch", type=int, choices=[0, 1, 2, 3], default=0,
+                    help="single problems: 0 the library's rule, 1 one CTA, 2 whole-GPU grid, "
+                         "3 one 8-CTA cluster")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true",
                     help="mpc_batch: skip the plain single-problem FP64 Lasso measurement")
@@ -841,7 +844,8 @@ def single_main(args, ws, rank, local, init_dist=True):
     cfg, desc, qp = build_problem(args, rank)
     prec = B.FP64 if args.precision == "fp64" else B.FP32_MIXED
     stream = torch.cuda.Stream()
-    s = Solver(qp, stream=stream.cuda_stream, precision=prec, autotune=args.autotune)
+    s = Solver(qp, stream=stream.cuda_stream, precision=prec, autotune=args.autotune,
+               launch=args.launch)
     groups = B.osqp_diag_schedule(s.handle)
     n, m = qp.n, qp.m
     dev = torch.device("cuda", local)
@@ -952,6 +956,9 @@ def single_main(args, ws, rank, local, init_dist=True):
         "config": {"workload": desc, "precision": args.precision, "eps": 1e-3,
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "parallelism": "replicas" if ws > 1 else "single",
+                   "team": {1: "one CTA", 2: "whole-GPU grid", 3: "8-CTA cluster"}.get(
+                       infos[-1].launch, str(infos[-1].launch))
+                   + (" (library rule)" if args.launch == 0 else " (--launch)"),
                    "row_groups": {"Kn": groups[0], "A": groups[1],
                                   "chosen_by": {1: "timing", 0: "rule"}.get(groups[2], "rule (timing failed)"),
                                   **({"ms_Kn": [round(v, 4) for v in groups[3]],
