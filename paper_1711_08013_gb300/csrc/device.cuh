@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include "dfloat.cuh"  // double-float arithmetic of the FP32-mixed CG scalars
 
 namespace osqpgb {
 
@@ -248,47 +249,6 @@ __device__ __forceinline__ float funkey(unsigned k) {
   return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
 }
 
-// Double-float arithmetic: a value held as the unevaluated sum h + l of two
-// floats with |l| ≤ ulp(h)/2, about 48 significant bits from FP32
-// instructions alone.  The error-free transformations are Knuth's TwoSum,
-// Dekker's FastTwoSum and the product error taken exactly by one fused
-// multiply-add; every operation is an explicitly rounded intrinsic, so the
-// compiler neither contracts nor reorders them.
-struct ff {
-  float h, l;
-};
-__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {  // |a| ≥ |b|
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ ff ff_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-// x − y; the closing TwoSum keeps the low part when the high parts cancel
-__device__ __forceinline__ ff ff_sub(ff x, ff y) {
-  const ff s = ff_two_sum(x.h, -y.h);
-  return ff_two_sum(s.h, __fadd_rn(s.l, __fsub_rn(x.l, y.l)));
-}
-__device__ __forceinline__ ff ff_mul(ff x, ff y) {
-  const float p = __fmul_rn(x.h, y.h);
-  float e = __fmaf_rn(x.h, y.h, -p);
-  e = __fmaf_rn(x.h, y.l, e);
-  e = __fmaf_rn(x.l, y.h, e);
-  return ff_fast_two_sum(p, e);
-}
-// x / y: the FP32 quotient, then one correction from the remainder x − q·y
-__device__ __forceinline__ ff ff_div(ff x, ff y) {
-  const float q = __fdiv_rn(x.h, y.h);
-  const ff r = ff_sub(x, ff_mul(y, ff{q, 0.0f}));
-  return ff_fast_two_sum(q, __fdiv_rn(r.h, y.h));
-}
-// the pair nearest to a double
-__device__ __forceinline__ ff ff_of(double x) {
-  const float h = (float)x;
-  return {h, (float)(x - (double)h)};
-}
 // result k of the last reduction as a double-float pair at kScalMirror
 __device__ __forceinline__ void mirror_store(double* sm, int k, ff v) {
   float* m = reinterpret_cast<float*>(sm + kScalOff + kScalMirror);
