@@ -37,3 +37,14 @@ def test_linear_in_iteration_counts(bench):
     assert f(10, 60, 2) - f(10, 60, 1) == pytest.approx(f(10, 60, 1) - f(10, 60, 0))
     # a check streams both matrices at least once in FP64 work
     assert f(10, 60, 1) - f(10, 60, 0) > 9000 * 12 + 6000 * 12
+
+
+def test_workload_text_states_its_parameters(bench):
+    """The serving line names the offered rate and the size cap it ran with,
+    in the bench's own line and in the reference arm's."""
+    import argparse
+    a = argparse.Namespace(nmax=500, rate=5.0)
+    text = bench.workload_desc(a, "serve")
+    assert "at 5 req/s" in text and "logU[10,500]" in text
+    assert "RATE" not in text and "NMAX" not in text
+    assert bench.workload_desc(a, "lasso") == bench.WORKLOADS["lasso"][1]
